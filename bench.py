@@ -1,0 +1,337 @@
+"""Throughput of the fused Abelian-Higgs leapfrog step on GB300.
+
+Workload (default): 1024^3 periodic lattice, float32 fields, radiation era (a ~ eta),
+s = 0, lambda0 = 2, e0 = 1, sigma = 1, dx = 0.5, dt = 0.1, random-phase initial
+condition (Sec. 2).  One benchmark step = one measurement period: 10 leapfrog steps
+(Eqs. 7-10) with the diagnostics of Eqs. diagxi / diagvel fused into the first of
+them, i.e. one ahs_step(h, 10) call.  Metric: lattice site-updates per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--size N]
+
+Under torchrun each rank advances an independent realisation (its own seed) on its
+own GPU: weak scaling, no collective on the data path; rank 0 prints one JSON line.
+The reference arm times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PERIOD = 10                     # leapfrog steps per benchmark step (measurement cadence)
+BYTES_PER_SITE = 80             # float32: read phi, Pi, theta, E (40 B) + write them (40 B)
+PARAMS = dict(dx=0.5, dt=0.1, lambda0=2.0, e0=1.0, sigma=1.0, s=0.0)
+ERA = 1                         # radiation
+
+
+def workload(N):
+    return {"workload": f"abelian-higgs leapfrog {N}^3 fp32, radiation era, s=0, lambda0=2, e0=1, "
+                        f"sigma=1, dx=0.5, dt=0.1, random-phase init, diagnostics fused every {PERIOD} steps",
+            "lattice": N, "leapfrog_steps_per_step": PERIOD, "era": "radiation", "s": 0.0,
+            "l2": "inputs larger than L2 (state %.1f GB resident in HBM)" % (N ** 3 * BYTES_PER_SITE / 1e9),
+            "parallelism": "replicas (one lattice per GPU)"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- helpers
+def kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2005_14454_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(N):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    per_site = d.get("dram_bytes_per_site")
+    return None if per_site is None else per_site * N ** 3
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+def cpu_baseline(seconds=12.0, N=128):
+    """The FP64 oracle as it stands, on this host's cores, over a bounded sample of
+    the workload: an N^3 lattice with the same couplings and era, leapfrog steps
+    until about `seconds` of CPU wall time have passed."""
+    import oracle
+    oracle.build()
+    p = oracle.Params(N=N, era=ERA, **PARAMS)
+    F = oracle.init(p, 1)
+    oracle.run(p, 0, 1, F)                       # warm-up (page-in, thread spin-up)
+    n, t0 = 1, time.perf_counter()
+    while True:
+        oracle.run(p, n, 1, F)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    steps = n - 1
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": N ** 3 * steps / dt, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, {N}^3 lattice of the same workload, {steps} leapfrog steps in {dt:.1f} s"}
+
+
+# --------------------------------------------------------------------- reference arm
+def run_reference(args, N):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    Ns = args.ref_size
+    p = oracle.Params(N=Ns, era=ERA, **PARAMS)
+    F = oracle.init(p, 1)
+    n = 0
+
+    def one_step():
+        nonlocal n
+        oracle.measure(p, n, F)                 # fused-measurement cadence of the engine
+        oracle.run(p, n, PERIOD, F)
+        n += PERIOD
+
+    for _ in range(args.warmup):
+        one_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one_step()
+    dt = time.perf_counter() - t0
+    value = Ns ** 3 * PERIOD * args.steps / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload(N),
+        "cpu_baseline": {"value": value, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"FP64 oracle on a {Ns}^3 lattice of the same workload: each step = "
+                                   f"one measurement + {PERIOD} leapfrog steps"},
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- our arm
+def run_ours(args, N):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2005_14454_gb300 import _abi
+    stream = torch.cuda.current_stream()
+    h = _abi.ahs_create(N, PARAMS["dx"], PARAMS["dt"], PARAMS["lambda0"], PARAMS["e0"], PARAMS["sigma"],
+                        PARAMS["s"], ERA)
+    _abi.ahs_set_stream(h, stream.cuda_stream)
+    _abi.ahs_set_option(h, _abi.AHS_OPT_MEASURE_EVERY, PERIOD)
+    _abi.ahs_init(h, 1000 + rank)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        _abi.ahs_step(h, PERIOD)
+    _abi.ahs_records(h)
+
+    # ---- device-timed region: inputs resident in HBM
+    _abi.ahs_set_option(h, _abi.AHS_OPT_PROFILE, 1)
+    _abi.ahs_kernel_time(h, _abi.AHS_KERNEL_STEP, reset=True)
+    _abi.ahs_kernel_time(h, _abi.AHS_KERNEL_STEP_MEASURE, reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _abi.ahs_step(h, PERIOD)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    k_ms, k_n = _abi.ahs_kernel_time(h, _abi.AHS_KERNEL_STEP)
+    km_ms, km_n = _abi.ahs_kernel_time(h, _abi.AHS_KERNEL_STEP_MEASURE)
+    _abi.ahs_set_option(h, _abi.AHS_OPT_PROFILE, 0)
+    recs = _abi.ahs_records(h)
+    nonfinite = any(r["nonfinite"] for r in recs)
+
+    # ---- end-to-end through the C ABI with host buffers: the initial state comes
+    # from pinned host memory, every step's measurement record goes back to the
+    # host, and the final state is copied back at the end.
+    e2e = None
+    if not args.no_e2e:
+        planes = 10
+        host = torch.empty((planes, N, N, N), dtype=torch.float32, pin_memory=True)
+        _abi.lib().ahs_fields(h, _abi.AHS_FIELD_ALL, host.data_ptr(), host.numel() * 4)
+        state_bytes = host.numel() * 4
+        barrier()
+        t0 = time.perf_counter()
+        _abi.check(_abi.lib().ahs_set_fields(h, _abi.AHS_FIELD_ALL, host.data_ptr(), state_bytes), "ahs_set_fields")
+        rec_bytes = 0
+        for _ in range(args.steps):
+            _abi.ahs_step(h, PERIOD)
+            rec_bytes += len(_abi.ahs_records(h)) * _abi.lib().ahs_sizeof_obs()
+        _abi.check(_abi.lib().ahs_fields(h, _abi.AHS_FIELD_ALL, host.data_ptr(), state_bytes), "ahs_fields")
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": ws * N ** 3 * PERIOD * args.steps / e2e_s, "unit": "site-updates/s",
+               "h2d_bytes_per_step": state_bytes / args.steps,
+               "d2h_bytes_per_step": (state_bytes + rec_bytes) / args.steps,
+               "note": "state uploaded from pinned host memory once, records read back every step, "
+                       "state read back at the end; per-step bytes are the totals / steps"}
+        del host
+
+    _abi.ahs_destroy(h)
+
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    value = ws * N ** 3 * PERIOD * args.steps / (ms / 1e3)
+    pk, pk_kind = peaks()
+    avg_ms = k_ms / max(k_n, 1)
+    bytes_per_launch = BYTES_PER_SITE * N ** 3
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    traffic = measured_traffic(N)
+    line = {
+        "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload(N),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                     "kernel": "step_kernel (plain leapfrog step)", "peak_kind": pk_kind,
+                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+                     "launches": k_n, "measure_kernel_avg_ms": km_ms / max(km_n, 1)},
+        "gpu_launches": args.steps * (PERIOD + 1),
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "nonfinite": nonfinite,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if dist is not None:
+        dist.destroy_process_group()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--size", type=int, default=1024)
+    ap.add_argument("--ref-size", type=int, default=128)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warm-up must be at least 3 steps", file=sys.stderr)
+        return 2
+    if args.impl == "reference":
+        return run_reference(args, args.size)
+    return run_ours(args, args.size)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * ahs.h -- C ABI of the GB300 engine for the lattice Abelian-Higgs string
+ * evolution of Correia & Martins, "Abelian-Higgs cosmic string evolution with
+ * multiple GPUs" (arXiv:2005.14454).
+ *
+ * One handle = one periodic comoving N^3 lattice on the current CUDA device:
+ * a complex scalar phi on sites and compact U(1) link angles theta_i = dx A_i
+ * (U_i = exp(-i theta_i), Eq. 13 with the dx of Eq. 16), evolved by the
+ * staggered leapfrog of Eqs. 7-10 in an expanding background a = (eta/eta0)^p
+ * with Crank-Nicolson damping (Eqs. 11-12), plus the string and velocity
+ * diagnostics of Eqs. diagxi and diagvel.
+ *
+ * Conventions
+ *  - Every function returns AHS_OK (0) or a negative status; ahs_create returns
+ *    NULL on error.  The status of the failing call on this thread is kept in
+ *    ahs_last_error(), with a message in ahs_last_error_message().  No C++
+ *    exception crosses the ABI.
+ *  - The library owns all device memory of a handle (cudaMalloc at create/init,
+ *    cudaFree at destroy).  The caller owns every host buffer it passes; the
+ *    library never keeps a host pointer after a call returns.
+ *  - Calls that move data or produce observables (init, step, measure, fields,
+ *    set_fields, windings, records) synchronise the handle's stream before they
+ *    return.  A handle is not thread-safe; distinct handles are independent.
+ *  - Field storage is float32, structure of arrays: one plane of N^3 values per
+ *    real component, site index x + N*(y + N*z) (x fastest).
+ */
+#ifndef AHS_H
+#define AHS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+enum {
+    AHS_OK = 0,
+    AHS_EINVAL = -1,      /* bad argument (size, selector, pointer, range)          */
+    AHS_ENOMEM = -2,      /* device or host allocation failed                       */
+    AHS_ECUDA = -3,       /* a CUDA runtime call failed; message has the CUDA error */
+    AHS_ESTATE = -4,      /* call not valid in the handle's state (e.g. not init)   */
+    AHS_ENONFINITE = -5,  /* a measurement found a non-finite field value           */
+    AHS_ETIMEOUT = -6     /* a bounded device-side wait gave up                      */
+};
+
+/* ---- expansion eras: the value is p in a = (eta/eta0)^p (Eq. defm in
+ *      conformal time; p = m/(1-m) for a physical-time exponent m) ------- */
+enum { AHS_MINKOWSKI = 0, AHS_RADIATION = 1, AHS_MATTER = 2 };
+
+/* ---- field selectors ------------------------------------------------------
+ * number of float32 planes: PHI 2 (Re, Im), PI 2 (Re, Im), THETA 3 (x, y, z),
+ * E 3 (x, y, z), ALL 10 in the order phi, Pi, theta, E.  phi and theta live at
+ * the integer time n, Pi and E at n - 1/2. */
+enum { AHS_FIELD_PHI = 0, AHS_FIELD_PI = 1, AHS_FIELD_THETA = 2, AHS_FIELD_E = 3,
+       AHS_FIELD_ALL = 4 };
+
+/* ---- options for ahs_set_option / ahs_get_option ------------------------ */
+enum {
+    AHS_OPT_MEASURE_EVERY = 0, /* fuse a measurement into every k-th step (0: never); default 10 */
+    AHS_OPT_ALPHA = 1,         /* damping form factor alpha of Eq. 11; default 2               */
+    AHS_OPT_TAU0 = 2,          /* initial conformal time eta0; default 1                       */
+    AHS_OPT_STEP = 3,          /* current integer time level n (eta = eta0 + n dt)             */
+    AHS_OPT_WRAP_THETA = 4,    /* 1: keep theta in (-pi, pi] after each drift; default 0       */
+    AHS_OPT_PROFILE = 5,       /* 1: time every step-kernel launch with CUDA events            */
+    AHS_OPT_N = 6              /* lattice side (read only)                                     */
+};
+
+typedef struct ahs ahs_t;
+
+/* ---- one measurement (all FP64 reductions) --------------------------------
+ * Taken at an integer time n from phi^n, theta^n and the momenta averaged over
+ * the kick of step n (Pibar = (Pi^{n-1/2} + Pi^{n+1/2})/2, Ebar likewise).
+ * Per site, with c = a^{2s}:
+ *   K = |Pibar|^2, G = sum_i |D_i^+ phi|^2, V = (lambda0 c/4)(|phi|^2 - sigma^2)^2,
+ *   El = sum_i Ebar_i^2/(2 e0^2 c), B = sum_{i<j} (1 - cos alpha_ij)/(e0^2 c dx^4),
+ *   L = K - G - V + El - B, rho = K + G + V + El + B, p = K - G/3 - V + (El+B)/3.
+ * xi_l = sqrt(-mu Vol/(dx^3 sum L)) with mu = 2 pi sigma^2 (Eq. diagxi, left);
+ * xi_w = sqrt(Vol/string_length), string_length = dx * n_wind, n_wind = sum |W_ij|
+ * over all plaquettes (Eq. diagxi, right); v2_phi = 2R/(1+R), R = sum K L/sum G L
+ * and v2_omega = (1 + 3 sum p L/sum rho L)/2 (Eq. diagvel, weight L).
+ * gauss_*: residual of Gauss's law (Eq. 5 in discrete form) of the stored
+ * momenta at n - 1/2 with phi^n.  nonfinite: number of sites whose diagnostic
+ * was not finite.  Energies carry the dx^3 volume factor; sum_* do not. */
+typedef struct ahs_obs {
+    int64_t step;
+    double tau, a;
+    int64_t n_wind;
+    double string_length, xi_w, xi_l, lagrangian;
+    double v2_phi, v2_omega;
+    double e_kin, e_grad, e_pot, e_elec, e_mag, e_total;
+    double gauss_rms, gauss_max;
+    int64_t nonfinite;
+    double sum_K, sum_G, sum_V, sum_El, sum_B, sum_L;
+    double sum_KL, sum_GL, sum_pL, sum_rhoL;
+} ahs_obs_t;
+
+/* ahs_create -- a lattice of side N (4 <= N <= 2048) with spacing dx, time step
+ * dt, couplings lambda0 and e0 (Eqs. 7-8), vacuum expectation value sigma, width
+ * exponent s (lambda = lambda0 a^{-2(1-s)}, e = e0 a^{-(1-s)}, so the potential
+ * and the current carry a^{2s}; Eq. 6 read with Eqs. 7-8), and era p in
+ * {0, 1, 2}.  Allocates 80 bytes of device memory per site: all ten field
+ * components double buffered, so a step reads one copy and writes the other.
+ * Fields are undefined until ahs_init or
+ * ahs_set_fields.  NULL on error (EINVAL, ENOMEM, ECUDA). */
+ahs_t *ahs_create(int N, double dx, double dt, double lambda0, double e0,
+                  double sigma, double s, int era);
+
+/* ahs_init -- random-phase initial condition of Sec. 2 at n = 0: phi(x) =
+ * sigma e^{i vartheta(x)}, Pi = theta = E = 0, with vartheta = 2 pi u and
+ * u = (sm64(seed ^ sm64(idx)) >> 11) 2^-53, sm64 one SplitMix64 step (Steele,
+ * Lea & Flood 2014); phase and cos/sin in FP64, stored rounded to float32.
+ * Clears the measurement log. */
+int ahs_init(ahs_t *h, uint64_t seed);
+
+/* ahs_step -- n >= 0 leapfrog steps (Eqs. 7-10): kick Pi and E at n -> n+1/2
+ * with the old phi, theta, then drift phi and theta to n+1.  Steps whose index
+ * is a multiple of AHS_OPT_MEASURE_EVERY also measure (fused into the same
+ * kernel) the state they start from and append the record to the log (see
+ * ahs_records).  Returns AHS_ENONFINITE (after completing all n steps) if any
+ * measurement of this call counted a non-finite site. */
+int ahs_step(ahs_t *h, int n);
+
+/* ahs_measure -- measure the current state (integer time n) without changing
+ * it: the kick of step n runs with its results kept in registers. */
+int ahs_measure(ahs_t *h, ahs_obs_t *out);
+
+/* ahs_records -- move up to max records of the measurement log (oldest first)
+ * into out; returns the number moved (>= 0) or a negative status.  out may be
+ * NULL with max 0 to query the number pending. */
+int ahs_records(ahs_t *h, ahs_obs_t *out, int max);
+
+/* ahs_fields / ahs_set_fields -- copy one field (see the selectors) between the
+ * device and a host buffer of exactly planes * N^3 * 4 bytes, planes in the
+ * selector's order.  set_fields leaves the time level n unchanged. */
+int ahs_fields(ahs_t *h, int which, void *host_dst, size_t bytes);
+int ahs_set_fields(ahs_t *h, int which, const void *host_src, size_t bytes);
+
+/* ahs_fields_box -- copy the periodic sub-box [x0, x0+nx) x [y0, y0+ny) x
+ * [z0, z0+nz) (coordinates taken modulo N, 1 <= n* <= N) of one field into a
+ * host buffer of planes * nx * ny * nz * 4 bytes, x fastest. */
+int ahs_fields_box(ahs_t *h, int which, int x0, int y0, int z0, int nx, int ny,
+                   int nz, void *host_dst, size_t bytes);
+
+/* ahs_windings -- the plaquette windings W_ij of the current state (gauge
+ * invariant form of Kajantie et al. 1998, cited for xi_W): 3 int8 planes
+ * (xy, xz, yz) of N^3, W_ij(x) for the plaquette with lower corner x.  bytes
+ * must be 3 * N^3.  Writes the total sum |W| to *n_wind when non-NULL. */
+int ahs_windings(ahs_t *h, int8_t *host_dst, size_t bytes, int64_t *n_wind);
+
+/* ahs_set_option / ahs_get_option -- see AHS_OPT_*.  Values are validated
+ * (EINVAL).  AHS_OPT_N is read only. */
+int ahs_set_option(ahs_t *h, int key, double value);
+int ahs_get_option(ahs_t *h, int key, double *value);
+
+/* ahs_set_stream -- run this handle's work on an existing CUDA stream
+ * (cudaStream_t passed as void*; NULL selects the legacy default stream).  The
+ * stream must belong to the device the handle was created on and outlive it. */
+int ahs_set_stream(ahs_t *h, void *cuda_stream);
+
+/* ahs_kernel_time -- with AHS_OPT_PROFILE on: total device time (ms, CUDA
+ * events recorded on the handle's stream around each launch) and number of
+ * launches of the step kernel since the last reset.  kind selects the plain
+ * step kernel (AHS_KERNEL_STEP) or the step kernel with the fused measurement
+ * (AHS_KERNEL_STEP_MEASURE); reset != 0 zeroes that counter after reading. */
+enum { AHS_KERNEL_STEP = 0, AHS_KERNEL_STEP_MEASURE = 1 };
+int ahs_kernel_time(ahs_t *h, int kind, double *ms_total, int64_t *launches, int reset);
+
+/* ahs_device_bytes -- device memory held by the handle. */
+int ahs_device_bytes(ahs_t *h, size_t *bytes);
+
+void ahs_destroy(ahs_t *h);
+
+int ahs_last_error(void);
+const char *ahs_last_error_message(void);
+const char *ahs_strerror(int status);
+size_t ahs_sizeof_obs(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AHS_H */

@@ -1,0 +1,99 @@
+"""GB300 engine for lattice Abelian-Higgs cosmic-string evolution.
+
+Implements the data-parallel hot path of Correia & Martins, "Abelian-Higgs cosmic
+string evolution with multiple GPUs" (arXiv:2005.14454): the staggered-leapfrog
+step of Eqs. 7-10 for a complex scalar and compact U(1) links on a periodic
+comoving lattice in an expanding background, with the string-winding, energy and
+velocity diagnostics of Eqs. diagxi / diagvel fused into it.
+
+The compute runs in hand-written sm_103a CUDA kernels behind the C ABI of
+``include/ahs.h`` (``_ahs.so``); this package is its ctypes binding plus a small
+object wrapper.  Build with ``paper_2005_14454_gb300.build.build()``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _abi
+from ._abi import (AHS_FIELD_ALL, AHS_FIELD_E, AHS_FIELD_PHI, AHS_FIELD_PI, AHS_FIELD_THETA,
+                   AHS_MATTER, AHS_MINKOWSKI, AHS_RADIATION, AHSError)
+
+ERAS = {"minkowski": AHS_MINKOWSKI, "radiation": AHS_RADIATION, "matter": AHS_MATTER}
+
+
+class Lattice:
+    """One N^3 lattice on the current CUDA device (owns its device memory)."""
+
+    def __init__(self, N: int, dx: float = 0.5, dt: float = 0.1, lambda0: float = 2.0,
+                 e0: float = 1.0, sigma: float = 1.0, s: float = 0.0, era=AHS_RADIATION,
+                 measure_every: int = 10, stream: int | None = None):
+        era = ERAS.get(era, era) if isinstance(era, str) else era
+        self.N = N
+        self.h = _abi.ahs_create(N, dx, dt, lambda0, e0, sigma, s, era)
+        _abi.ahs_set_option(self.h, _abi.AHS_OPT_MEASURE_EVERY, measure_every)
+        if stream is not None:
+            _abi.ahs_set_stream(self.h, stream)
+
+    # lifecycle ---------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            _abi.ahs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # evolution -----------------------------------------------------------------
+    def init(self, seed: int):
+        _abi.ahs_init(self.h, seed)
+
+    def step(self, n: int = 1):
+        _abi.ahs_step(self.h, n)
+
+    def measure(self) -> dict:
+        return _abi.ahs_measure(self.h)
+
+    def records(self):
+        return _abi.ahs_records(self.h)
+
+    @property
+    def n(self) -> int:
+        return int(_abi.ahs_get_option(self.h, _abi.AHS_OPT_STEP))
+
+    @n.setter
+    def n(self, value: int):
+        _abi.ahs_set_option(self.h, _abi.AHS_OPT_STEP, value)
+
+    def set_option(self, key: int, value: float):
+        _abi.ahs_set_option(self.h, key, value)
+
+    # data movement -------------------------------------------------------------
+    def state(self) -> np.ndarray:
+        """All ten planes (Re phi, Im phi, Re Pi, Im Pi, theta_xyz, E_xyz) as float32
+        of shape (10, N, N, N) indexed [plane, z, y, x]."""
+        return _abi.ahs_fields(self.h, AHS_FIELD_ALL)
+
+    def set_state(self, F: np.ndarray):
+        _abi.ahs_set_fields(self.h, AHS_FIELD_ALL, np.ascontiguousarray(F, dtype=np.float32))
+
+    def field(self, which: int) -> np.ndarray:
+        return _abi.ahs_fields(self.h, which)
+
+    def box(self, which: int, x0: int, y0: int, z0: int, nx: int, ny: int, nz: int) -> np.ndarray:
+        return _abi.ahs_fields_box(self.h, which, x0, y0, z0, nx, ny, nz)
+
+    def windings(self):
+        return _abi.ahs_windings(self.h)
+
+
+__all__ = ["Lattice", "AHSError", "ERAS", "AHS_FIELD_ALL", "AHS_FIELD_E", "AHS_FIELD_PHI",
+           "AHS_FIELD_PI", "AHS_FIELD_THETA", "AHS_MATTER", "AHS_MINKOWSKI", "AHS_RADIATION"]

@@ -1,0 +1,548 @@
+// ahs_abi.cu -- host side of the C ABI declared in include/ahs.h.
+//
+// Owns the device state of one lattice, turns the step index into the FP64
+// scalars of Eqs. 7-8 and 11-12 (rounded once to float32 for the stencil), and
+// sequences the step, reduction and copy launches on the handle's stream.
+#include "ahs_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace eng;
+
+namespace {
+
+thread_local int g_last = AHS_OK;
+thread_local char g_msg[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    g_last = code;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int ok()
+{
+    g_last = AHS_OK;
+    g_msg[0] = 0;
+    return AHS_OK;
+}
+
+#define CU(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fail(AHS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr double kPi = 3.141592653589793238;
+constexpr int kFields = 10;   // Re phi, Im phi, Re Pi, Im Pi, theta_xyz, E_xyz
+
+}  // namespace
+
+struct ahs {
+    int N = 0;
+    size_t V = 0;
+    double dx = 0.5, dt = 0.1, lambda0 = 2.0, e0 = 1.0, sigma = 1.0, s = 0.0;
+    int era = 1;
+    double alpha = 2.0, tau0 = 1.0;
+    int measure_every = 10;
+    int wrap = 0;
+    int profile = 0;
+    int64_t n = 0;        // integer time level of phi/theta in buffer `cur`
+    int cur = 0;
+    bool ready = false;   // fields defined
+    int device = 0;
+
+    float *base = nullptr;           // 2 * kFields planes of V floats
+    double *partials = nullptr;      // step_blocks(N) * NQ
+    int nblocks = 0;
+    ahs_obs_t *rec_dev = nullptr;    // device records of one ahs_step call
+    int rec_cap = 0;
+    ahs_obs_t *rec_host = nullptr;   // pinned staging
+    std::vector<ahs_obs_t> log;
+
+    cudaStream_t stream = nullptr;
+    std::vector<cudaEvent_t> ev;     // profiling event pool (pairs)
+    double prof_ms[2] = {0.0, 0.0};  // [plain step, measuring step]
+    int64_t prof_launches[2] = {0, 0};
+
+    float *plane(int buf, int f) const { return base + ((size_t)buf * kFields + f) * V; }
+};
+
+namespace {
+
+// FP64 scalars of step n (Eqs. 7, 8, 11, 12): eta, a, delta, omega, c = a^{2s}
+struct Scalars {
+    double eta, a, delta, omega, c;
+};
+
+Scalars scalars(const ahs_t *h, int64_t n)
+{
+    Scalars r;
+    r.eta = h->tau0 + (double)n * h->dt;
+    r.a = std::pow(r.eta / h->tau0, (double)h->era);
+    r.delta = 0.5 * h->alpha * (double)h->era * h->dt / r.eta;
+    r.omega = r.delta * (1.0 - h->s);
+    r.c = std::pow(r.a, 2.0 * h->s);
+    return r;
+}
+
+StepCoef coefficients(const ahs_t *h, int64_t n)
+{
+    const Scalars S = scalars(h, n);
+    const double dx = h->dx, dt = h->dt;
+    StepCoef k;
+    k.cpi = (float)((1.0 - S.delta) / (1.0 + S.delta));
+    k.kpi_lap = (float)(dt / ((1.0 + S.delta) * dx * dx));
+    k.kpi_pot = (float)(dt * 0.5 * h->lambda0 * S.c / (1.0 + S.delta));
+    k.sigma2 = (float)(h->sigma * h->sigma);
+    k.ce = (float)((1.0 - S.omega) / (1.0 + S.omega));
+    k.ke_curl = (float)(dt / ((1.0 + S.omega) * dx * dx * dx));
+    k.ke_cur = (float)(dt * 2.0 * h->e0 * h->e0 * S.c / ((1.0 + S.omega) * dx));
+    k.dphi = (float)dt;
+    k.dtheta = (float)(dt * dx);
+    k.wrap = h->wrap;
+    k.m_grad = (float)(1.0 / (dx * dx));
+    k.m_pot = (float)(0.25 * h->lambda0 * S.c);
+    k.m_el = (float)(1.0 / (2.0 * h->e0 * h->e0 * S.c));
+    k.m_mag = (float)(1.0 / (h->e0 * h->e0 * S.c * dx * dx * dx * dx));
+    const Scalars P = scalars(h, n - 1);   // the kick that produced the stored momenta
+    const double kappa = P.c * (1.0 + P.delta) / (1.0 + P.omega);
+    k.m_gauss = (float)(2.0 * h->e0 * h->e0 * kappa);
+    k.inv_dx = (float)(1.0 / dx);
+    return k;
+}
+
+StepPtrs pointers(const ahs_t *h)
+{
+    const int a = h->cur, b = 1 - h->cur;
+    StepPtrs p;
+    p.pr = h->plane(a, 0); p.pim = h->plane(a, 1);
+    p.qr = h->plane(a, 2); p.qi = h->plane(a, 3);
+    p.tx = h->plane(a, 4); p.ty = h->plane(a, 5); p.tz = h->plane(a, 6);
+    p.ex = h->plane(a, 7); p.ey = h->plane(a, 8); p.ez = h->plane(a, 9);
+    p.pr1 = h->plane(b, 0); p.pim1 = h->plane(b, 1);
+    p.qr1 = h->plane(b, 2); p.qi1 = h->plane(b, 3);
+    p.tx1 = h->plane(b, 4); p.ty1 = h->plane(b, 5); p.tz1 = h->plane(b, 6);
+    p.ex1 = h->plane(b, 7); p.ey1 = h->plane(b, 8); p.ez1 = h->plane(b, 9);
+    return p;
+}
+
+ObsScalars obs_scalars(const ahs_t *h, int64_t n)
+{
+    const Scalars S = scalars(h, n);
+    ObsScalars o;
+    o.step = n;
+    o.tau = S.eta;
+    o.a = S.a;
+    o.dx = h->dx;
+    o.sites = (double)h->V;
+    o.volume = std::pow((double)h->N * h->dx, 3.0);
+    o.mu = 2.0 * kPi * h->sigma * h->sigma;
+    return o;
+}
+
+// field selector -> (first plane, number of planes)
+bool selector(int which, int *first, int *count)
+{
+    switch (which) {
+    case AHS_FIELD_PHI: *first = 0; *count = 2; return true;
+    case AHS_FIELD_PI: *first = 2; *count = 2; return true;
+    case AHS_FIELD_THETA: *first = 4; *count = 3; return true;
+    case AHS_FIELD_E: *first = 7; *count = 3; return true;
+    case AHS_FIELD_ALL: *first = 0; *count = 10; return true;
+    default: return false;
+    }
+}
+
+int ensure_records(ahs_t *h, int count)
+{
+    if (count <= h->rec_cap) return AHS_OK;
+    int cap = h->rec_cap ? h->rec_cap : 64;
+    while (cap < count) cap *= 2;
+    if (h->rec_dev) cudaFree(h->rec_dev);
+    if (h->rec_host) cudaFreeHost(h->rec_host);
+    h->rec_dev = nullptr;
+    h->rec_host = nullptr;
+    h->rec_cap = 0;
+    if (cudaMalloc(&h->rec_dev, sizeof(ahs_obs_t) * cap) != cudaSuccess)
+        return fail(AHS_ENOMEM, "cannot allocate %d device records", cap);
+    if (cudaMallocHost(&h->rec_host, sizeof(ahs_obs_t) * cap) != cudaSuccess)
+        return fail(AHS_ENOMEM, "cannot allocate %d pinned records", cap);
+    h->rec_cap = cap;
+    return AHS_OK;
+}
+
+cudaEvent_t event_at(ahs_t *h, size_t i)
+{
+    while (h->ev.size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev.push_back(e);
+    }
+    return h->ev[i];
+}
+
+int set_device(const ahs_t *h)
+{
+    CU(cudaSetDevice(h->device));
+    return AHS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ahs_last_error(void) { return g_last; }
+const char *ahs_last_error_message(void) { return g_msg; }
+size_t ahs_sizeof_obs(void) { return sizeof(ahs_obs_t); }
+
+const char *ahs_strerror(int status)
+{
+    switch (status) {
+    case AHS_OK: return "ok";
+    case AHS_EINVAL: return "invalid argument";
+    case AHS_ENOMEM: return "out of memory";
+    case AHS_ECUDA: return "CUDA error";
+    case AHS_ESTATE: return "invalid state";
+    case AHS_ENONFINITE: return "non-finite field value";
+    case AHS_ETIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+    }
+}
+
+ahs_t *ahs_create(int N, double dx, double dt, double lambda0, double e0, double sigma, double s, int era)
+{
+    if (N < 4 || N > 2048) { fail(AHS_EINVAL, "N=%d outside [4, 2048]", N); return nullptr; }
+    if (!(dx > 0) || !(dt > 0) || !std::isfinite(dx) || !std::isfinite(dt)) {
+        fail(AHS_EINVAL, "dx and dt must be positive");
+        return nullptr;
+    }
+    if (!std::isfinite(lambda0) || !std::isfinite(e0) || !(e0 != 0) || !std::isfinite(sigma) || !std::isfinite(s)) {
+        fail(AHS_EINVAL, "couplings must be finite and e0 non-zero");
+        return nullptr;
+    }
+    if (era < 0 || era > 2) { fail(AHS_EINVAL, "era=%d not in {0,1,2}", era); return nullptr; }
+    ahs_t *h = new (std::nothrow) ahs_t;
+    if (!h) { fail(AHS_ENOMEM, "host allocation"); return nullptr; }
+    h->N = N;
+    h->V = (size_t)N * N * N;
+    h->dx = dx; h->dt = dt; h->lambda0 = lambda0; h->e0 = e0; h->sigma = sigma; h->s = s; h->era = era;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        fail(AHS_ECUDA, "no CUDA device");
+        delete h;
+        return nullptr;
+    }
+    const size_t bytes = sizeof(float) * h->V * 2 * kFields;
+    cudaError_t e = cudaMalloc(&h->base, bytes);
+    if (e != cudaSuccess) {
+        fail(e == cudaErrorMemoryAllocation ? AHS_ENOMEM : AHS_ECUDA, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+        cudaGetLastError();
+        delete h;
+        return nullptr;
+    }
+    h->nblocks = step_blocks(N);
+    e = cudaMalloc(&h->partials, sizeof(double) * NQ * (size_t)h->nblocks);
+    if (e != cudaSuccess) {
+        fail(AHS_ENOMEM, "cudaMalloc(partials): %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        cudaFree(h->base);
+        delete h;
+        return nullptr;
+    }
+    if (ensure_records(h, 64) != AHS_OK) {
+        cudaFree(h->partials);
+        cudaFree(h->base);
+        delete h;
+        return nullptr;
+    }
+    ok();
+    return h;
+}
+
+void ahs_destroy(ahs_t *h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->rec_dev) cudaFree(h->rec_dev);
+    if (h->rec_host) cudaFreeHost(h->rec_host);
+    if (h->partials) cudaFree(h->partials);
+    if (h->base) cudaFree(h->base);
+    delete h;
+}
+
+int ahs_set_stream(ahs_t *h, void *stream)
+{
+    if (!h) return fail(AHS_EINVAL, "null handle");
+    h->stream = (cudaStream_t)stream;
+    return ok();
+}
+
+int ahs_device_bytes(ahs_t *h, size_t *bytes)
+{
+    if (!h || !bytes) return fail(AHS_EINVAL, "null argument");
+    *bytes = sizeof(float) * h->V * 2 * kFields + sizeof(double) * NQ * (size_t)h->nblocks +
+             sizeof(ahs_obs_t) * (size_t)h->rec_cap;
+    return ok();
+}
+
+int ahs_init(ahs_t *h, uint64_t seed)
+{
+    if (!h) return fail(AHS_EINVAL, "null handle");
+    if (int r = set_device(h)) return r;
+    h->cur = 0;
+    h->n = 0;
+    CU(cudaMemsetAsync(h->plane(0, 2), 0, sizeof(float) * h->V * 8, h->stream));
+    CU(launch_init(h->plane(0, 0), h->plane(0, 1), h->N, seed, h->sigma, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    h->ready = true;
+    h->log.clear();
+    return ok();
+}
+
+int ahs_set_option(ahs_t *h, int key, double v)
+{
+    if (!h) return fail(AHS_EINVAL, "null handle");
+    switch (key) {
+    case AHS_OPT_MEASURE_EVERY:
+        if (!(v >= 0) || v > 1e9 || v != std::floor(v)) return fail(AHS_EINVAL, "measure_every must be a non-negative integer");
+        h->measure_every = (int)v;
+        return ok();
+    case AHS_OPT_ALPHA:
+        if (!std::isfinite(v)) return fail(AHS_EINVAL, "alpha must be finite");
+        h->alpha = v;
+        return ok();
+    case AHS_OPT_TAU0:
+        if (!(v > 0) || !std::isfinite(v)) return fail(AHS_EINVAL, "tau0 must be positive");
+        h->tau0 = v;
+        return ok();
+    case AHS_OPT_STEP:
+        if (v != std::floor(v) || std::fabs(v) > 9e15) return fail(AHS_EINVAL, "step must be an integer");
+        h->n = (int64_t)v;
+        return ok();
+    case AHS_OPT_WRAP_THETA:
+        if (v != 0 && v != 1) return fail(AHS_EINVAL, "wrap_theta must be 0 or 1");
+        h->wrap = (int)v;
+        return ok();
+    case AHS_OPT_PROFILE:
+        if (v != 0 && v != 1) return fail(AHS_EINVAL, "profile must be 0 or 1");
+        h->profile = (int)v;
+        return ok();
+    case AHS_OPT_N:
+        return fail(AHS_EINVAL, "N is read only");
+    default:
+        return fail(AHS_EINVAL, "unknown option %d", key);
+    }
+}
+
+int ahs_get_option(ahs_t *h, int key, double *v)
+{
+    if (!h || !v) return fail(AHS_EINVAL, "null argument");
+    switch (key) {
+    case AHS_OPT_MEASURE_EVERY: *v = h->measure_every; break;
+    case AHS_OPT_ALPHA: *v = h->alpha; break;
+    case AHS_OPT_TAU0: *v = h->tau0; break;
+    case AHS_OPT_STEP: *v = (double)h->n; break;
+    case AHS_OPT_WRAP_THETA: *v = h->wrap; break;
+    case AHS_OPT_PROFILE: *v = h->profile; break;
+    case AHS_OPT_N: *v = h->N; break;
+    default: return fail(AHS_EINVAL, "unknown option %d", key);
+    }
+    return ok();
+}
+
+int ahs_step(ahs_t *h, int nsteps)
+{
+    if (!h) return fail(AHS_EINVAL, "null handle");
+    if (nsteps < 0) return fail(AHS_EINVAL, "negative step count");
+    if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
+    if (int r = set_device(h)) return r;
+    int nrec = 0;
+    if (h->measure_every > 0) {
+        for (int i = 0; i < nsteps; ++i)
+            if ((h->n + i) % h->measure_every == 0) ++nrec;
+    }
+    if (int r = ensure_records(h, nrec)) return r;
+    size_t nev = 0;
+    int ri = 0;
+    std::vector<char> kind;          // per event pair: 1 if the launch measured
+    for (int i = 0; i < nsteps; ++i) {
+        const bool meas = h->measure_every > 0 && (h->n % h->measure_every == 0);
+        const StepCoef k = coefficients(h, h->n);
+        const StepPtrs p = pointers(h);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->profile) {
+            e0 = event_at(h, nev++);
+            e1 = event_at(h, nev++);
+            kind.push_back(meas ? 1 : 0);
+            if (!e0 || !e1) return fail(AHS_ECUDA, "cudaEventCreate failed");
+            CU(cudaEventRecord(e0, h->stream));
+        }
+        int nb = 0;
+        CU(launch_step(p, k, h->N, meas, true, h->partials, &nb, h->stream));
+        if (h->profile) CU(cudaEventRecord(e1, h->stream));
+        if (meas) {
+            CU(launch_reduce(h->partials, nb, obs_scalars(h, h->n), h->rec_dev + ri, h->stream));
+            ++ri;
+        }
+        h->cur = 1 - h->cur;
+        h->n += 1;
+    }
+    if (ri > 0) CU(cudaMemcpyAsync(h->rec_host, h->rec_dev, sizeof(ahs_obs_t) * ri, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (h->profile) {
+        for (size_t j = 0; j + 1 < nev; j += 2) {
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, h->ev[j], h->ev[j + 1]));
+            h->prof_ms[(int)kind[j / 2]] += ms;
+            h->prof_launches[(int)kind[j / 2]] += 1;
+        }
+    }
+    bool bad = false;
+    for (int j = 0; j < ri; ++j) {
+        h->log.push_back(h->rec_host[j]);
+        if (h->rec_host[j].nonfinite != 0) bad = true;
+    }
+    if (bad) return fail(AHS_ENONFINITE, "a measurement counted non-finite sites");
+    return ok();
+}
+
+int ahs_measure(ahs_t *h, ahs_obs_t *out)
+{
+    if (!h || !out) return fail(AHS_EINVAL, "null argument");
+    if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
+    if (int r = set_device(h)) return r;
+    const StepCoef k = coefficients(h, h->n);
+    const StepPtrs p = pointers(h);
+    int nb = 0;
+    CU(launch_step(p, k, h->N, true, false, h->partials, &nb, h->stream));
+    CU(launch_reduce(h->partials, nb, obs_scalars(h, h->n), h->rec_dev, h->stream));
+    CU(cudaMemcpyAsync(h->rec_host, h->rec_dev, sizeof(ahs_obs_t), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    *out = h->rec_host[0];
+    return ok();
+}
+
+int ahs_records(ahs_t *h, ahs_obs_t *out, int max)
+{
+    if (!h) return fail(AHS_EINVAL, "null handle");
+    if (max < 0 || (max > 0 && !out)) return fail(AHS_EINVAL, "bad output buffer");
+    if (max == 0) {
+        ok();
+        return (int)h->log.size();
+    }
+    const int m = (int)h->log.size() < max ? (int)h->log.size() : max;
+    for (int i = 0; i < m; ++i) out[i] = h->log[i];
+    h->log.erase(h->log.begin(), h->log.begin() + m);
+    ok();
+    return m;
+}
+
+int ahs_fields(ahs_t *h, int which, void *dst, size_t bytes)
+{
+    if (!h || !dst) return fail(AHS_EINVAL, "null argument");
+    int first, count;
+    if (!selector(which, &first, &count)) return fail(AHS_EINVAL, "unknown field selector %d", which);
+    if (bytes != sizeof(float) * h->V * count)
+        return fail(AHS_EINVAL, "buffer is %zu bytes, field needs %zu", bytes, sizeof(float) * h->V * count);
+    if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
+    if (int r = set_device(h)) return r;
+    for (int i = 0; i < count; ++i)
+        CU(cudaMemcpyAsync((float *)dst + (size_t)i * h->V, h->plane(h->cur, first + i), sizeof(float) * h->V,
+                           cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return ok();
+}
+
+int ahs_set_fields(ahs_t *h, int which, const void *src, size_t bytes)
+{
+    if (!h || !src) return fail(AHS_EINVAL, "null argument");
+    int first, count;
+    if (!selector(which, &first, &count)) return fail(AHS_EINVAL, "unknown field selector %d", which);
+    if (bytes != sizeof(float) * h->V * count)
+        return fail(AHS_EINVAL, "buffer is %zu bytes, field needs %zu", bytes, sizeof(float) * h->V * count);
+    if (int r = set_device(h)) return r;
+    if (!h->ready) {
+        // a partial set on a fresh handle leaves the other fields zero
+        CU(cudaMemsetAsync(h->plane(h->cur, 0), 0, sizeof(float) * h->V * kFields, h->stream));
+    }
+    for (int i = 0; i < count; ++i)
+        CU(cudaMemcpyAsync(h->plane(h->cur, first + i), (const float *)src + (size_t)i * h->V, sizeof(float) * h->V,
+                           cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    h->ready = true;
+    return ok();
+}
+
+int ahs_fields_box(ahs_t *h, int which, int x0, int y0, int z0, int nx, int ny, int nz, void *dst, size_t bytes)
+{
+    if (!h || !dst) return fail(AHS_EINVAL, "null argument");
+    int first, count;
+    if (!selector(which, &first, &count)) return fail(AHS_EINVAL, "unknown field selector %d", which);
+    const int N = h->N;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > N || ny > N || nz > N) return fail(AHS_EINVAL, "box extent outside [1, N]");
+    const size_t per = (size_t)nx * ny * nz;
+    if (bytes != sizeof(float) * per * count) return fail(AHS_EINVAL, "buffer is %zu bytes, box needs %zu", bytes, sizeof(float) * per * count);
+    if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
+    if (int r = set_device(h)) return r;
+    auto md = [N](int v) { v %= N; return v < 0 ? v + N : v; };
+    const float *planes[10];
+    for (int i = 0; i < count; ++i) planes[i] = h->plane(h->cur, first + i);
+    float *tmp = nullptr;
+    CU(cudaMallocAsync(&tmp, sizeof(float) * per * count, h->stream));
+    cudaError_t e = launch_gather_box(planes, count, N, md(x0), md(y0), md(z0), nx, ny, nz, tmp, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(tmp, h->stream);
+    if (e != cudaSuccess) return fail(AHS_ECUDA, "box copy: %s", cudaGetErrorString(e));
+    CU(cudaStreamSynchronize(h->stream));
+    return ok();
+}
+
+int ahs_windings(ahs_t *h, int8_t *dst, size_t bytes, int64_t *n_wind)
+{
+    if (!h || !dst) return fail(AHS_EINVAL, "null argument");
+    if (bytes != 3 * h->V) return fail(AHS_EINVAL, "buffer is %zu bytes, windings need %zu", bytes, 3 * h->V);
+    if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
+    if (int r = set_device(h)) return r;
+    int8_t *W = nullptr;
+    CU(cudaMallocAsync(&W, bytes, h->stream));
+    const int c = h->cur;
+    cudaError_t e = launch_windings(h->plane(c, 0), h->plane(c, 1), h->plane(c, 4), h->plane(c, 5), h->plane(c, 6), h->N,
+                                    W, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, W, bytes, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(W, h->stream);
+    if (e != cudaSuccess) return fail(AHS_ECUDA, "windings: %s", cudaGetErrorString(e));
+    CU(cudaStreamSynchronize(h->stream));
+    if (n_wind) {
+        int64_t t = 0;
+        for (size_t i = 0; i < bytes; ++i) t += dst[i] < 0 ? -dst[i] : dst[i];
+        *n_wind = t;
+    }
+    return ok();
+}
+
+int ahs_kernel_time(ahs_t *h, int kind, double *ms, int64_t *launches, int reset)
+{
+    if (!h) return fail(AHS_EINVAL, "null handle");
+    if (kind != AHS_KERNEL_STEP && kind != AHS_KERNEL_STEP_MEASURE) return fail(AHS_EINVAL, "unknown kernel kind %d", kind);
+    if (ms) *ms = h->prof_ms[kind];
+    if (launches) *launches = h->prof_launches[kind];
+    if (reset) {
+        h->prof_ms[kind] = 0.0;
+        h->prof_launches[kind] = 0;
+    }
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// ahs_internal.cuh -- shared declarations of the GB300 engine (kernels + host ABI).
+//
+// Lattice Abelian-Higgs evolution of Correia & Martins (arXiv:2005.14454), Sec. 2:
+// staggered leapfrog (Eqs. 7-10), covariant Laplacian (Eq. 14), plaquettes
+// (Eqs. 15-16), diagnostics (Eqs. diagxi, diagvel).  Storage is float32 SoA,
+// site index x + N*(y + N*z).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ahs.h"
+
+namespace eng {
+
+// ---- reduction slots of one measurement (per-block FP64 partials) ----------
+enum {
+    Q_K = 0, Q_G, Q_V, Q_EL, Q_B, Q_L, Q_KL, Q_GL, Q_PL, Q_RL,  // site sums
+    Q_G2,      // sum of squared Gauss residual
+    Q_GMAX,    // max |Gauss residual|
+    Q_WIND,    // sum |W_ij| over plaquettes
+    Q_NF,      // sites with a non-finite diagnostic
+    NQ = 16
+};
+constexpr int NSUM = 11;   // slots Q_K..Q_G2 are plain sums
+
+// Device pointers of one step.  Every field is double buffered: the step reads
+// phi^n, theta^n, Pi^{n-1/2}, E^{n-1/2} from one buffer and writes phi^{n+1},
+// theta^{n+1}, Pi^{n+1/2}, E^{n+1/2} into the other, so no thread ever reads a
+// value another thread of the same launch has already replaced.
+struct StepPtrs {
+    const float *pr, *pim, *tx, *ty, *tz, *qr, *qi, *ex, *ey, *ez;
+    float *pr1, *pim1, *tx1, *ty1, *tz1, *qr1, *qi1, *ex1, *ey1, *ez1;
+};
+
+// Per-step coefficients, computed in FP64 on the host from the step index and
+// rounded once to float32.
+//   Pi^{n+1/2} = cpi Pi + kpi_lap (sum_i [U phi(x+i) + U^* phi(x-i)] - 6 phi)
+//                - kpi_pot (|phi|^2 - sigma^2) phi                       (Eq. 7)
+//   E_i^{n+1/2} = ce E_i + ke_curl (curl of sin alpha)_i + ke_cur J_i     (Eq. 8)
+//   phi += dphi Pi, theta_i += dtheta E_i                               (Eqs. 9-10)
+struct StepCoef {
+    float cpi, kpi_lap, kpi_pot, sigma2;
+    float ce, ke_curl, ke_cur;
+    float dphi, dtheta;
+    int wrap;
+    // measurement factors (Eqs. diagxi, diagvel and the Gauss residual)
+    float m_grad;   // 1/dx^2
+    float m_pot;    // lambda0 c / 4
+    float m_el;     // 1/(2 e0^2 c)
+    float m_mag;    // 1/(e0^2 c dx^4)
+    float m_gauss;  // 2 e0^2 kappa_{n-1}
+    float inv_dx;
+};
+
+// Scalars the final reduction needs to turn sums into an observable record.
+struct ObsScalars {
+    int64_t step;
+    double tau, a, dx, sites, volume, mu;
+};
+
+// Launchers (ahs_kernels.cu).  All take the stream they run on.
+cudaError_t launch_init(float *pr, float *pim, int N, uint64_t seed, double sigma, cudaStream_t st);
+cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, bool measure, bool store,
+                        double *partials, int *nblocks, cudaStream_t st);
+int step_blocks(int N);   // number of partial-sum blocks launch_step writes
+cudaError_t launch_reduce(const double *partials, int nblocks, const ObsScalars &sc,
+                          ahs_obs_t *rec, cudaStream_t st);
+cudaError_t launch_windings(const float *pr, const float *pim, const float *tx, const float *ty,
+                            const float *tz, int N, int8_t *W, cudaStream_t st);
+cudaError_t launch_gather_box(const float *const *planes, int nplanes, int N, int x0, int y0, int z0,
+                              int nx, int ny, int nz, float *dst, cudaStream_t st);
+
+}  // namespace eng

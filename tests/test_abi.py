@@ -1,0 +1,77 @@
+"""Host-side checks of the C ABI that need no GPU: the shared library loads, exports
+every entry point include/ahs.h declares, and rejects bad arguments before any
+CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_2005_14454_gb300 import build, _abi
+    build.build()
+    return _abi
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "ahs.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ahs_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    for want in ("ahs_create", "ahs_init", "ahs_step", "ahs_measure", "ahs_fields", "ahs_destroy"):
+        assert want in syms
+
+
+def test_library_exports_every_declared_symbol(abi):
+    L = abi.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+    assert set(declared_symbols()) <= set(abi.EXPORTS) | {"ahs_create"}
+
+
+def test_obs_layout(abi):
+    assert abi.lib().ahs_sizeof_obs() == ctypes.sizeof(abi.ahs_obs_t)
+
+
+def test_strerror(abi):
+    L = abi.lib()
+    assert L.ahs_strerror(0) == b"ok"
+    assert L.ahs_strerror(abi.AHS_EINVAL) == b"invalid argument"
+    assert L.ahs_strerror(abi.AHS_ENONFINITE) == b"non-finite field value"
+    assert L.ahs_strerror(12345) == b"unknown status"
+
+
+@pytest.mark.parametrize("args", [
+    (3, 0.5, 0.1, 2.0, 1.0, 1.0, 0.0, 1),        # N too small
+    (4096, 0.5, 0.1, 2.0, 1.0, 1.0, 0.0, 1),     # N too large
+    (16, -0.5, 0.1, 2.0, 1.0, 1.0, 0.0, 1),      # dx <= 0
+    (16, 0.5, 0.0, 2.0, 1.0, 1.0, 0.0, 1),       # dt <= 0
+    (16, 0.5, 0.1, 2.0, 0.0, 1.0, 0.0, 1),       # e0 = 0
+    (16, 0.5, 0.1, 2.0, 1.0, 1.0, 0.0, 3),       # unknown era
+    (16, 0.5, 0.1, float("nan"), 1.0, 1.0, 0.0, 1),
+])
+def test_create_rejects_bad_arguments(abi, args):
+    L = abi.lib()
+    assert not L.ahs_create(*args)
+    assert L.ahs_last_error() == abi.AHS_EINVAL
+    assert L.ahs_last_error_message()
+
+
+def test_null_handle_is_rejected(abi):
+    L = abi.lib()
+    assert L.ahs_init(None, 1) == abi.AHS_EINVAL
+    assert L.ahs_step(None, 1) == abi.AHS_EINVAL
+    assert L.ahs_set_option(None, 0, 1.0) == abi.AHS_EINVAL
+    L.ahs_destroy(None)
+
+
+def test_binding_raises_without_library(tmp_path, abi):
+    with pytest.raises(ImportError):
+        abi.load(str(tmp_path / "missing.so"))

@@ -1,0 +1,287 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (float32 storage and arithmetic against FP64):
+* fields after 10 leapfrog steps from identical float32 states: relative L2 error
+  <= 1e-5 per field group (phi, Pi, theta via exp(-i theta), E);
+* windings on identical snapshots: bit-exact, per plaquette;
+* observables on identical snapshots: sums of non-negative site terms to 2e-5
+  relative; signed or ratio observables to 2e-4 relative (per-site float32
+  rounding ~1e-7 amplified by cancellation between the Lagrangian's terms);
+* Gauss residual: float32 rounding level on both sides (same snapshot).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = dict(dx=0.5, dt=0.1, lambda0=2.0, e0=1.0, sigma=1.0)
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2005_14454_gb300 import _abi
+    import paper_2005_14454_gb300 as pkg
+    _abi.lib()
+    return pkg
+
+
+def lattice(eng, N, era=1, s=0.0, measure_every=0, **kw):
+    p = dict(PARAMS)
+    p.update(kw)
+    return eng.Lattice(N, era=era, s=s, measure_every=measure_every, **p)
+
+
+def oparams(orc, N, era=1, s=0.0, **kw):
+    p = dict(PARAMS)
+    p.update(kw)
+    return orc.Params(N=N, era=era, s=s, **p)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def field_errors(got, ref):
+    return {
+        "phi": rel(got[0:2], ref[0:2]),
+        "Pi": rel(got[2:4], ref[2:4]),
+        "theta": np.linalg.norm(np.exp(-1j * got[4:7]) - np.exp(-1j * ref[4:7])) / max(np.linalg.norm(ref[4:7]), 1e-3 * math.sqrt(ref[4:7].size)),
+        "E": rel(got[7:10], ref[7:10]),
+    }
+
+
+# ------------------------------------------------------------------ init
+@pytest.mark.parametrize("N", [4, 24, 40, 64])
+def test_init_matches_oracle(eng, orc, N):
+    with lattice(eng, N) as lat:
+        lat.init(99)
+        F = lat.state().astype(np.float64)
+    ref = orc.init(oparams(orc, N), 99)
+    ref32 = ref.astype(np.float32).astype(np.float64)
+    assert not F[2:].any()
+    diff = np.abs(F - ref32)
+    # FP64 cos/sin of the GPU and of libm may differ in the last bit, which changes
+    # the float32 rounding only next to a rounding boundary
+    assert diff.max() <= 1.2e-7
+    assert (diff > 0).sum() <= max(2, F.size // 100000)
+
+
+# ------------------------------------------------------------------ evolution
+CASES = [
+    (8, 1, 0.0), (24, 1, 0.0), (40, 1, 0.0), (64, 1, 0.0),   # radiation, several tiles, ragged
+    (24, 2, 0.0), (24, 0, 0.0), (36, 2, 1.0), (20, 1, 1.0),  # matter, Minkowski, s = 1
+]
+
+
+@pytest.mark.parametrize("N,era,s", CASES)
+def test_ten_steps_match_oracle(eng, orc, N, era, s):
+    with lattice(eng, N, era=era, s=s) as lat:
+        lat.init(2024 + N)
+        F0 = lat.state().astype(np.float64)
+        lat.step(10)
+        got = lat.state().astype(np.float64)
+        assert lat.n == 10
+    ref = F0.copy()
+    orc.run(oparams(orc, N, era=era, s=s), 0, 10, ref)
+    err = field_errors(got, ref)
+    assert max(err.values()) < 1e-5, err
+
+
+def test_perturbed_state_with_gauge_fields(eng, orc):
+    # nonzero theta, E, Pi from the start (all force terms active in step 1)
+    N = 32
+    F0 = inputs.to_f32(inputs.perturbed_state(N, 5, amp_theta=0.6, amp_e=0.4)).astype(np.float64)
+    with lattice(eng, N, era=2) as lat:
+        lat.set_state(F0)
+        lat.n = 3
+        lat.step(10)
+        got = lat.state().astype(np.float64)
+    ref = F0.copy()
+    orc.run(oparams(orc, N, era=2), 3, 10, ref)
+    err = field_errors(got, ref)
+    assert max(err.values()) < 1e-5, err
+
+
+def test_vacuum_is_exact_fixed_point(eng):
+    N = 16
+    F = np.zeros((10, N, N, N), np.float32)
+    F[0] = 1.0
+    with lattice(eng, N, era=2) as lat:
+        lat.set_state(F)
+        lat.step(7)
+        assert np.array_equal(lat.state(), F)
+
+
+# ------------------------------------------------------------------ windings
+@pytest.mark.parametrize("N,steps", [(24, 15), (64, 30)])
+def test_windings_bit_exact_on_identical_snapshot(eng, orc, N, steps):
+    with lattice(eng, N) as lat:
+        lat.init(7)
+        lat.step(steps)
+        snap = lat.state().astype(np.float64)
+        W, n = lat.windings()
+        obs = lat.measure()
+    Wo, no = orc.windings(oparams(orc, N), snap)
+    assert no > 0
+    assert np.array_equal(W, Wo)
+    assert n == no == obs["n_wind"]
+
+
+def test_vortex_pair_windings(eng):
+    N = 32
+    F = inputs.with_phase(inputs.vortex_pair_phase(N))
+    chi = inputs.gauge_function(N, 4)
+    e = np.exp(1j * chi)
+    phi = (F[0] + 1j * F[1]) * e
+    F[0], F[1] = phi.real, phi.imag
+    for i, ax in enumerate((2, 1, 0)):
+        F[4 + i] = np.roll(chi, -1, axis=ax) - chi
+    with lattice(eng, N) as lat:
+        lat.set_state(F)
+        W, n = lat.windings()
+        obs = lat.measure()
+    assert n == 2 * N and obs["n_wind"] == 2 * N
+    (x1, y1), (x2, y2) = inputs.vortex_pair_cores(N)
+    assert (W[0, :, y1, x1] == 1).all() and (W[0, :, y2, x2] == -1).all()
+
+
+# ------------------------------------------------------------------ measurement
+SUMS = ("sum_K", "sum_G", "sum_V", "sum_El", "sum_B", "e_total")
+SIGNED = ("lagrangian", "xi_l", "v2_phi", "v2_omega", "sum_KL", "sum_GL", "sum_pL", "sum_rhoL")
+
+
+@pytest.mark.parametrize("N,era,s,steps", [(32, 1, 0.0, 12), (48, 2, 0.0, 25), (24, 1, 1.0, 5)])
+def test_measure_matches_oracle_on_identical_snapshot(eng, orc, N, era, s, steps):
+    with lattice(eng, N, era=era, s=s) as lat:
+        lat.init(31)
+        lat.step(steps)
+        snap = lat.state().astype(np.float64)
+        obs = lat.measure()
+        assert lat.n == steps
+    o = orc.measure(oparams(orc, N, era=era, s=s), steps, snap)
+    assert obs["step"] == steps and obs["tau"] == pytest.approx(o["tau"]) and obs["a"] == pytest.approx(o["a"])
+    for k in SUMS:
+        assert obs[k] == pytest.approx(o[k], rel=2e-5), k
+    for k in SIGNED:
+        assert obs[k] == pytest.approx(o[k], rel=2e-4), k
+    assert obs["n_wind"] == o["n_wind"]
+    assert obs["xi_w"] == pytest.approx(o["xi_w"], rel=1e-12)
+    assert obs["nonfinite"] == 0
+    # Gauss residual of a float32-evolved snapshot sits at float32 rounding; both
+    # sides evaluate it on the same snapshot, the engine in float32
+    scale = np.abs(snap[7:10]).max() / PARAMS["dx"] + np.abs(snap[2:4]).max() + 1.0
+    assert o["gauss_max"] < 1e-5 * scale
+    assert obs["gauss_max"] < 1e-5 * scale
+    assert abs(obs["gauss_rms"] - o["gauss_rms"]) < 1e-6 * scale
+
+
+def test_fused_records_equal_standalone_measure(eng):
+    N = 32
+    with lattice(eng, N, measure_every=10) as lat:
+        lat.init(3)
+        lat.step(10)
+        standalone = lat.measure()
+        lat.step(15)
+        recs = lat.records()
+    assert [r["step"] for r in recs] == [0, 10, 20]
+    assert recs[1] == standalone
+
+
+def test_step_zero_and_records_drain(eng):
+    with lattice(eng, 16, measure_every=3) as lat:
+        lat.init(1)
+        lat.step(0)
+        assert lat.records() == []
+        lat.step(7)
+        assert [r["step"] for r in lat.records()] == [0, 3, 6]
+        assert lat.records() == []
+
+
+def test_nonfinite_is_reported(eng):
+    from paper_2005_14454_gb300 import AHSError
+    from paper_2005_14454_gb300._abi import AHS_ENONFINITE
+    N = 16
+    F = inputs.to_f32(inputs.perturbed_state(N, 2))
+    F[7, 3, 4, 5] = np.nan
+    with lattice(eng, N, measure_every=1) as lat:
+        lat.set_state(F)
+        with pytest.raises(AHSError) as ei:
+            lat.step(2)
+        assert ei.value.status == AHS_ENONFINITE
+        assert lat.n == 2
+        assert lat.measure()["nonfinite"] > 0
+
+
+# ------------------------------------------------------------------ data movement
+def test_resume_is_bit_exact(eng):
+    N = 24
+    with lattice(eng, N) as a:
+        a.init(77)
+        a.step(20)
+        full = a.state()
+    with lattice(eng, N) as b:
+        b.init(77)
+        b.step(10)
+        snap = b.state()
+    with lattice(eng, N) as c:
+        c.set_state(snap)
+        c.n = 10
+        c.step(10)
+        assert np.array_equal(c.state(), full)
+
+
+def test_fields_box_periodic(eng):
+    N = 20
+    F = inputs.to_f32(inputs.perturbed_state(N, 9))
+    with lattice(eng, N) as lat:
+        lat.set_state(F)
+        from paper_2005_14454_gb300 import AHS_FIELD_ALL, AHS_FIELD_THETA
+        B = lat.box(AHS_FIELD_ALL, 17, 3, 19, 6, 5, 4)
+        T = lat.box(AHS_FIELD_THETA, -2, 0, 0, N, 1, 1)
+    xs, ys, zs = (np.arange(17, 23) % N), (np.arange(3, 8) % N), (np.arange(19, 23) % N)
+    want = F[:, zs][:, :, ys][:, :, :, xs]
+    assert np.array_equal(B, want)
+    assert np.array_equal(T[:, 0, 0, :], F[4:7, 0, 0, (np.arange(-2, N - 2) % N)])
+
+
+def test_bad_buffers_rejected(eng):
+    from paper_2005_14454_gb300 import AHSError, _abi
+    with lattice(eng, 8) as lat:
+        with pytest.raises(AHSError):
+            lat.step(1)                                  # not initialised
+        lat.init(1)
+        with pytest.raises(AHSError):
+            _abi.ahs_set_fields(lat.h, 0, np.zeros(10, np.float32))
+        with pytest.raises(AHSError):
+            _abi.ahs_set_option(lat.h, _abi.AHS_OPT_MEASURE_EVERY, -1)
+        with pytest.raises(AHSError):
+            lat.box(0, 0, 0, 0, 9, 1, 1)
+
+
+# ------------------------------------------------------------------ full size
+def test_full_size_sampled_sites(eng, orc):
+    """1024^3 in the launch configuration the benchmark times: one step from the
+    random-phase start and one from a later state, checked at sampled sites
+    against the oracle run on the 5^3 periodic neighbourhood of each site (the
+    update of a site reads only its nearest and next-nearest neighbours)."""
+    N = 1024
+    rng = np.random.default_rng(0)
+    sites = [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(12)]
+    sites += [(0, 0, 0), (N - 1, N - 1, N - 1), (0, N - 1, 511), (N - 1, 0, 0)]
+    from paper_2005_14454_gb300 import AHS_FIELD_ALL
+    with lattice(eng, N, measure_every=0) as lat:
+        lat.init(1)
+        lat.step(3)
+        before = [lat.box(AHS_FIELD_ALL, x - 2, y - 2, z - 2, 5, 5, 5).astype(np.float64) for (x, y, z) in sites]
+        lat.step(1)
+        after = [lat.box(AHS_FIELD_ALL, x, y, z, 1, 1, 1).astype(np.float64)[:, 0, 0, 0] for (x, y, z) in sites]
+    p = oparams(orc, 5)
+    for B, A in zip(before, after):
+        ref = B.copy()
+        orc.run(p, 3, 1, ref)
+        r = ref[:, 2, 2, 2]
+        assert np.allclose(A, r, rtol=2e-6, atol=2e-6), (A, r)
