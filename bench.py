@@ -214,7 +214,11 @@ def run_ours(args, N):
                         PARAMS["s"], ERA)
     _abi.ahs_set_stream(h, stream.cuda_stream)
     _abi.ahs_set_option(h, _abi.AHS_OPT_MEASURE_EVERY, PERIOD)
+    _abi.ahs_set_option(h, _abi.AHS_OPT_TILE_Y, args.tile_y)
+    _abi.ahs_set_option(h, _abi.AHS_OPT_ZCHUNK, args.zchunk)
     _abi.ahs_init(h, 1000 + rank)
+    shape = {"tile": [32, int(_abi.ahs_get_option(h, _abi.AHS_OPT_TILE_Y))],
+             "zchunk": int(_abi.ahs_get_option(h, _abi.AHS_OPT_ZCHUNK))}
 
     def barrier():
         if dist is not None:
@@ -298,9 +302,10 @@ def run_ours(args, N):
         "data": "synthetic", "config": workload(N),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                     "kernel": "step_kernel (plain leapfrog step)", "peak_kind": pk_kind,
+                     "kernel": "step_tiled (plain leapfrog step)", "peak_kind": pk_kind,
                      "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
-                     "launches": k_n, "measure_kernel_avg_ms": km_ms / max(km_n, 1)},
+                     "launches": k_n, "measure_kernel_avg_ms": km_ms / max(km_n, 1),
+                     "launch_shape": shape},
         "gpu_launches": args.steps * (PERIOD + 1),
         "clocks": clocks.summary(),
         "e2e": e2e,
@@ -322,6 +327,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--ref-size", type=int, default=128)
+    ap.add_argument("--tile-y", type=int, default=0, help="step-kernel tile height (8, 16; 0 = auto)")
+    ap.add_argument("--zchunk", type=int, default=0, help="z planes per CTA (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     args = ap.parse_args()

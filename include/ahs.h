@@ -64,7 +64,9 @@ enum {
     AHS_OPT_STEP = 3,          /* current integer time level n (eta = eta0 + n dt)             */
     AHS_OPT_WRAP_THETA = 4,    /* 1: keep theta in (-pi, pi] after each drift; default 0       */
     AHS_OPT_PROFILE = 5,       /* 1: time every step-kernel launch with CUDA events            */
-    AHS_OPT_N = 6              /* lattice side (read only)                                     */
+    AHS_OPT_N = 6,             /* lattice side (read only)                                     */
+    AHS_OPT_TILE_Y = 7,        /* step-kernel tile height: 8 or 16 rows of 32 sites; 0 = auto   */
+    AHS_OPT_ZCHUNK = 8         /* z planes one CTA marches through, 1..N; 0 = auto            */
 };
 
 typedef struct ahs ahs_t;

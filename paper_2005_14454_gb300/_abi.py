@@ -19,7 +19,7 @@ AHS_MINKOWSKI, AHS_RADIATION, AHS_MATTER = 0, 1, 2
 AHS_FIELD_PHI, AHS_FIELD_PI, AHS_FIELD_THETA, AHS_FIELD_E, AHS_FIELD_ALL = 0, 1, 2, 3, 4
 FIELD_PLANES = {AHS_FIELD_PHI: 2, AHS_FIELD_PI: 2, AHS_FIELD_THETA: 3, AHS_FIELD_E: 3, AHS_FIELD_ALL: 10}
 (AHS_OPT_MEASURE_EVERY, AHS_OPT_ALPHA, AHS_OPT_TAU0, AHS_OPT_STEP, AHS_OPT_WRAP_THETA,
- AHS_OPT_PROFILE, AHS_OPT_N) = range(7)
+ AHS_OPT_PROFILE, AHS_OPT_N, AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK) = range(9)
 AHS_KERNEL_STEP, AHS_KERNEL_STEP_MEASURE = 0, 1
 
 # every symbol include/ahs.h declares

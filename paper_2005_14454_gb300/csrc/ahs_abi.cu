@@ -62,8 +62,9 @@ struct ahs {
     int device = 0;
 
     float *base = nullptr;           // 2 * kFields planes of V floats
-    double *partials = nullptr;      // step_blocks(N) * NQ
-    int nblocks = 0;
+    double *partials = nullptr;      // nblocks * NQ
+    int nblocks = 0;                 // capacity of partials in rows
+    int tile_y = 0, zchunk = 0;      // launch-shape overrides (0: automatic)
     ahs_obs_t *rec_dev = nullptr;    // device records of one ahs_step call
     int rec_cap = 0;
     ahs_obs_t *rec_host = nullptr;   // pinned staging
@@ -181,6 +182,23 @@ int ensure_records(ahs_t *h, int count)
     return AHS_OK;
 }
 
+// grow the measurement partials to the CTA count of the current launch shape
+int ensure_partials(ahs_t *h, int blocks)
+{
+    if (blocks <= h->nblocks) return AHS_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->partials);
+    h->partials = nullptr;
+    h->nblocks = 0;
+    if (cudaMalloc(&h->partials, sizeof(double) * NQ * (size_t)blocks) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(AHS_ENOMEM, "cannot allocate %d measurement partials", blocks);
+    }
+    h->nblocks = blocks;
+    return AHS_OK;
+}
+
 cudaEvent_t event_at(ahs_t *h, size_t i)
 {
     while (h->ev.size() <= i) {
@@ -249,7 +267,7 @@ ahs_t *ahs_create(int N, double dx, double dt, double lambda0, double e0, double
         delete h;
         return nullptr;
     }
-    h->nblocks = step_blocks(N);
+    h->nblocks = step_shape(N, 0, 0).blocks;
     e = cudaMalloc(&h->partials, sizeof(double) * NQ * (size_t)h->nblocks);
     if (e != cudaSuccess) {
         fail(AHS_ENOMEM, "cudaMalloc(partials): %s", cudaGetErrorString(e));
@@ -339,6 +357,14 @@ int ahs_set_option(ahs_t *h, int key, double v)
         if (v != 0 && v != 1) return fail(AHS_EINVAL, "profile must be 0 or 1");
         h->profile = (int)v;
         return ok();
+    case AHS_OPT_TILE_Y:
+        if (v != 0 && v != 8 && v != 16) return fail(AHS_EINVAL, "tile_y must be 0, 8 or 16");
+        h->tile_y = (int)v;
+        return ok();
+    case AHS_OPT_ZCHUNK:
+        if (!(v >= 0) || v > h->N || v != std::floor(v)) return fail(AHS_EINVAL, "zchunk must be an integer in [0, N]");
+        h->zchunk = (int)v;
+        return ok();
     case AHS_OPT_N:
         return fail(AHS_EINVAL, "N is read only");
     default:
@@ -357,6 +383,8 @@ int ahs_get_option(ahs_t *h, int key, double *v)
     case AHS_OPT_WRAP_THETA: *v = h->wrap; break;
     case AHS_OPT_PROFILE: *v = h->profile; break;
     case AHS_OPT_N: *v = h->N; break;
+    case AHS_OPT_TILE_Y: *v = step_shape(h->N, h->tile_y, h->zchunk).by; break;
+    case AHS_OPT_ZCHUNK: *v = step_shape(h->N, h->tile_y, h->zchunk).dz; break;
     default: return fail(AHS_EINVAL, "unknown option %d", key);
     }
     return ok();
@@ -374,6 +402,7 @@ int ahs_step(ahs_t *h, int nsteps)
             if ((h->n + i) % h->measure_every == 0) ++nrec;
     }
     if (int r = ensure_records(h, nrec)) return r;
+    if (int r = ensure_partials(h, step_shape(h->N, h->tile_y, h->zchunk).blocks)) return r;
     size_t nev = 0;
     int ri = 0;
     std::vector<char> kind;          // per event pair: 1 if the launch measured
@@ -389,8 +418,9 @@ int ahs_step(ahs_t *h, int nsteps)
             if (!e0 || !e1) return fail(AHS_ECUDA, "cudaEventCreate failed");
             CU(cudaEventRecord(e0, h->stream));
         }
-        int nb = 0;
-        CU(launch_step(p, k, h->N, meas, true, h->partials, &nb, h->stream));
+        const StepShape sh = step_shape(h->N, h->tile_y, h->zchunk);
+        const int nb = sh.blocks;
+        CU(launch_step(p, k, h->N, sh, meas, true, h->partials, h->stream));
         if (h->profile) CU(cudaEventRecord(e1, h->stream));
         if (meas) {
             CU(launch_reduce(h->partials, nb, obs_scalars(h, h->n), h->rec_dev + ri, h->stream));
@@ -423,10 +453,12 @@ int ahs_measure(ahs_t *h, ahs_obs_t *out)
     if (!h || !out) return fail(AHS_EINVAL, "null argument");
     if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
     if (int r = set_device(h)) return r;
+    if (int r = ensure_partials(h, step_shape(h->N, h->tile_y, h->zchunk).blocks)) return r;
     const StepCoef k = coefficients(h, h->n);
     const StepPtrs p = pointers(h);
-    int nb = 0;
-    CU(launch_step(p, k, h->N, true, false, h->partials, &nb, h->stream));
+    const StepShape sh = step_shape(h->N, h->tile_y, h->zchunk);
+    const int nb = sh.blocks;
+    CU(launch_step(p, k, h->N, sh, true, false, h->partials, h->stream));
     CU(launch_reduce(h->partials, nb, obs_scalars(h, h->n), h->rec_dev, h->stream));
     CU(cudaMemcpyAsync(h->rec_host, h->rec_dev, sizeof(ahs_obs_t), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));

@@ -1,0 +1,149 @@
+// ahs_device.cuh -- device helpers shared by the engine's kernels: the gauge-
+// invariant link phase and plaquette wrap of the winding count, and site indexing.
+#pragma once
+
+#include "ahs_internal.cuh"
+
+namespace eng {
+
+constexpr float kPiF = 3.14159265358979f;
+constexpr float kTwoPiF = 6.28318530717959f;
+constexpr float kInvTwoPiF = 0.159154943091895f;
+constexpr double kPiD = 3.141592653589793238;
+// Below pi - kTie the float32 branch decision of atan2 / of the wrap is the same
+// as the FP64 one (the float32 error is < 1e-6 rad); at and above it the value is
+// recomputed in FP64 with the operations in the order of the definition.
+constexpr float kTie = 1e-4f;
+
+// ---------------------------------------------------------------- windings
+// Y_i(x) = arg(phi^*(x) U_i(x) phi(x+i)), U_i = exp(-i theta_i).
+static __device__ __noinline__ double link_phase_fp64(float pr, float pi, float qr, float qi, float th)
+{
+    double s, c;
+    sincos((double)th, &s, &c);
+    double ur = c, ui = -s;
+    double hr = __dsub_rn(__dmul_rn(ur, (double)qr), __dmul_rn(ui, (double)qi));
+    double hi = __dadd_rn(__dmul_rn(ur, (double)qi), __dmul_rn(ui, (double)qr));
+    double zr = __dsub_rn(__dmul_rn((double)pr, hr), __dmul_rn(-(double)pi, hi));
+    double zi = __dadd_rn(__dmul_rn((double)pr, hi), __dmul_rn(-(double)pi, hr));
+    return atan2(zi, zr);
+}
+
+static __device__ __forceinline__ float link_phase(float pr, float pi, float qr, float qi, float th)
+{
+    float s, c;
+    sincosf(th, &s, &c);
+    float hr = c * qr + s * qi;
+    float hi = c * qi - s * qr;
+    float zr = pr * hr + pi * hi;
+    float zi = pr * hi - pi * hr;
+    float y = atan2f(zi, zr);
+    if (fabsf(y) > kPiF - kTie) y = (float)link_phase_fp64(pr, pi, qr, qi, th);
+    return y;
+}
+
+// [alpha]_pi of alpha = a + b - c - d: wrapped into (-pi, pi] by
+// alpha + 2 pi floor((pi - alpha)/(2 pi)).
+static __device__ __noinline__ double wrap_plaq_fp64(float a, float b, float c, float d)
+{
+    double al = __dsub_rn(__dsub_rn(__dadd_rn((double)a, (double)b), (double)c), (double)d);
+    double k = floor(__ddiv_rn(__dsub_rn(kPiD, al), 2.0 * kPiD));
+    return __dadd_rn(al, __dmul_rn(2.0 * kPiD, k));
+}
+
+static __device__ __forceinline__ float wrap_plaq(float a, float b, float c, float d)
+{
+    float al = ((a + b) - c) - d;
+    float w = al + kTwoPiF * floorf((kPiF - al) * kInvTwoPiF);
+    float mag = fabsf(a) + fabsf(b) + fabsf(c) + fabsf(d);
+    if (fabsf(w) > kPiF - (kTie + 1e-6f * mag)) w = (float)wrap_plaq_fp64(a, b, c, d);
+    return w;
+}
+
+
+// Y_i(x) from a precomputed link phase V_i = (cos theta_i, sin theta_i) = conj(U_i);
+// the FP64 fallback recomputes from theta itself.
+static __device__ __forceinline__ float link_phase_v(float pr, float pi, float qr, float qi, float vc, float vs,
+                                                     float th)
+{
+    const float hr = vc * qr + vs * qi;   // U_i q with U_i = vc - i vs
+    const float hi = vc * qi - vs * qr;
+    const float zr = pr * hr + pi * hi;   // conj(p) U_i q
+    const float zi = pr * hi - pi * hr;
+    float y = atan2f(zi, zr);
+    if (fabsf(y) > kPiF - kTie) y = (float)link_phase_fp64(pr, pi, qr, qi, th);
+    return y;
+}
+
+// [alpha]_pi from the plaquette product Q = exp(i alpha) (Eq. 15 conjugated); the
+// FP64 fallback recomputes alpha = a + b - c - d from the four link angles.
+static __device__ __forceinline__ float wrap_from_q(float qr, float qi, float a, float b, float c, float d)
+{
+    float w = atan2f(qi, qr);
+    if (fabsf(w) > kPiF - kTie) w = (float)wrap_plaq_fp64(a, b, c, d);
+    return w;
+}
+
+static __device__ __forceinline__ int winding(float y1, float y2, float y3, float y4, float aw)
+{
+    float sum = ((((y1 + y2) - y3) - y4) + aw);
+    return __float2int_rn(sum * kInvTwoPiF);
+}
+
+static __device__ __forceinline__ size_t sidx(int x, int y, int z, int N)
+{
+    return (size_t)x + (size_t)N * ((size_t)y + (size_t)N * (size_t)z);
+}
+
+// ---------------------------------------------------------------- reduction
+struct Acc {
+    float s[NSUM];
+    float gmax;
+    int wind, nf;
+};
+
+static __device__ __forceinline__ void acc_zero(Acc &a)
+{
+#pragma unroll
+    for (int q = 0; q < NSUM; ++q) a.s[q] = 0.f;
+    a.gmax = 0.f;
+    a.wind = 0;
+    a.nf = 0;
+}
+
+// Block reduction of Acc to one row of FP64 partials: float32 within a warp,
+// FP64 across warps in a fixed order (deterministic for a fixed launch shape).
+template <int NT>
+static __device__ void block_reduce_store(Acc &a, double *out)
+{
+    constexpr int NW = NT / 32;
+    __shared__ double red[NW][NQ];
+    const int lane = threadIdx.x & 31;
+    const int wid = (threadIdx.x + blockDim.x * threadIdx.y) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NSUM; ++q) a.s[q] += __shfl_xor_sync(0xffffffffu, a.s[q], off);
+        a.gmax = fmaxf(a.gmax, __shfl_xor_sync(0xffffffffu, a.gmax, off));
+        a.wind += __shfl_xor_sync(0xffffffffu, a.wind, off);
+        a.nf += __shfl_xor_sync(0xffffffffu, a.nf, off);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NSUM; ++q) red[wid][q] = (double)a.s[q];
+        red[wid][Q_GMAX] = (double)a.gmax;
+        red[wid][Q_WIND] = (double)a.wind;
+        red[wid][Q_NF] = (double)a.nf;
+        red[wid][14] = 0.0;
+        red[wid][15] = 0.0;
+    }
+    __syncthreads();
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;
+    if (t < NQ) {
+        double v = red[0][t];
+        for (int w = 1; w < NW; ++w) v = (t == Q_GMAX) ? fmax(v, red[w][t]) : v + red[w][t];
+        out[t] = v;
+    }
+}
+
+}  // namespace eng

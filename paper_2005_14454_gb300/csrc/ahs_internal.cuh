@@ -62,9 +62,14 @@ struct ObsScalars {
 
 // Launchers (ahs_kernels.cu).  All take the stream they run on.
 cudaError_t launch_init(float *pr, float *pim, int N, uint64_t seed, double sigma, cudaStream_t st);
-cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, bool measure, bool store,
-                        double *partials, int *nblocks, cudaStream_t st);
-int step_blocks(int N);   // number of partial-sum blocks launch_step writes
+// Launch shape of the z-marching step kernel: tile height (8 or 16 rows of 32
+// sites), z-chunk per CTA, and the number of CTAs (= rows of measurement partials).
+struct StepShape {
+    int by, dz, blocks;
+};
+StepShape step_shape(int N, int tile_y, int zchunk);   // tile_y/zchunk 0: automatic
+cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, bool measure, bool store,
+                        double *partials, cudaStream_t st);
 cudaError_t launch_reduce(const double *partials, int nblocks, const ObsScalars &sc,
                           ahs_obs_t *rec, cudaStream_t st);
 cudaError_t launch_windings(const float *pr, const float *pim, const float *tx, const float *ty,

@@ -72,6 +72,7 @@ def test_init_matches_oracle(eng, orc, N):
 
 # ------------------------------------------------------------------ evolution
 CASES = [
+    (4, 1, 0.0), (5, 1, 0.0), (7, 2, 0.0),                  # smaller than one tile, odd N
     (8, 1, 0.0), (24, 1, 0.0), (40, 1, 0.0), (64, 1, 0.0),   # radiation, several tiles, ragged
     (24, 2, 0.0), (24, 0, 0.0), (36, 2, 1.0), (20, 1, 1.0),  # matter, Minkowski, s = 1
 ]
@@ -89,6 +90,30 @@ def test_ten_steps_match_oracle(eng, orc, N, era, s):
     orc.run(oparams(orc, N, era=era, s=s), 0, 10, ref)
     err = field_errors(got, ref)
     assert max(err.values()) < 1e-5, err
+
+
+@pytest.mark.parametrize("N", [20, 40, 64])
+def test_launch_shapes_give_identical_fields(eng, N):
+    # every link phase and plaquette is computed by the same arithmetic whatever the
+    # tile height and z-chunk, so the fields agree bit for bit; the reductions
+    # differ only in grouping
+    from paper_2005_14454_gb300._abi import AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK
+    outs, recs = [], []
+    for by, dz in [(8, 0), (16, 0), (8, 5), (16, 3), (8, N), (16, 1)]:
+        with lattice(eng, N, measure_every=3) as lat:
+            lat.set_option(AHS_OPT_TILE_Y, by)
+            lat.set_option(AHS_OPT_ZCHUNK, dz)
+            lat.init(5)
+            lat.step(7)
+            outs.append(lat.state())
+            recs.append(lat.records())
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+    for r in recs[1:]:
+        for a, b in zip(r, recs[0]):
+            assert a["n_wind"] == b["n_wind"]
+            assert a["e_total"] == pytest.approx(b["e_total"], rel=1e-6)
+            assert a["lagrangian"] == pytest.approx(b["lagrangian"], rel=1e-5)
 
 
 def test_perturbed_state_with_gauge_fields(eng, orc):
