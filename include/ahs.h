@@ -98,7 +98,7 @@ typedef struct ahs_obs {
     double sum_KL, sum_GL, sum_pL, sum_rhoL;
 } ahs_obs_t;
 
-/* ahs_create -- a lattice of side N (4 <= N <= 2048) with spacing dx, time step
+/* ahs_create -- a lattice of side N (4 <= N <= 1600, so N^3 < 2^32) with spacing dx, time step
  * dt, couplings lambda0 and e0 (Eqs. 7-8), vacuum expectation value sigma, width
  * exponent s (lambda = lambda0 a^{-2(1-s)}, e = e0 a^{-(1-s)}, so the potential
  * and the current carry a^{2s}; Eq. 6 read with Eqs. 7-8), and era p in

@@ -239,7 +239,7 @@ const char *ahs_strerror(int status)
 
 ahs_t *ahs_create(int N, double dx, double dt, double lambda0, double e0, double sigma, double s, int era)
 {
-    if (N < 4 || N > 2048) { fail(AHS_EINVAL, "N=%d outside [4, 2048]", N); return nullptr; }
+    if (N < 4 || N > 1600) { fail(AHS_EINVAL, "N=%d outside [4, 1600]", N); return nullptr; }
     if (!(dx > 0) || !(dt > 0) || !std::isfinite(dx) || !std::isfinite(dt)) {
         fail(AHS_EINVAL, "dx and dt must be positive");
         return nullptr;

@@ -10,9 +10,10 @@ constexpr float kPiF = 3.14159265358979f;
 constexpr float kTwoPiF = 6.28318530717959f;
 constexpr float kInvTwoPiF = 0.159154943091895f;
 constexpr double kPiD = 3.141592653589793238;
-// Below pi - kTie the float32 branch decision of atan2 / of the wrap is the same
-// as the FP64 one (the float32 error is < 1e-6 rad); at and above it the value is
-// recomputed in FP64 with the operations in the order of the definition.
+// A float32 complex number whose imaginary part exceeds kTie times its real part
+// has the same sign as its FP64 counterpart (float32 errors are ~1e-7 relative),
+// so its arg lies on the same side of the branch cut; closer to the cut the value
+// is recomputed in FP64 with the operations in the order of the definition.
 constexpr float kTie = 1e-4f;
 
 // ---------------------------------------------------------------- windings
@@ -29,19 +30,6 @@ static __device__ __noinline__ double link_phase_fp64(float pr, float pi, float 
     return atan2(zi, zr);
 }
 
-static __device__ __forceinline__ float link_phase(float pr, float pi, float qr, float qi, float th)
-{
-    float s, c;
-    sincosf(th, &s, &c);
-    float hr = c * qr + s * qi;
-    float hi = c * qi - s * qr;
-    float zr = pr * hr + pi * hi;
-    float zi = pr * hi - pi * hr;
-    float y = atan2f(zi, zr);
-    if (fabsf(y) > kPiF - kTie) y = (float)link_phase_fp64(pr, pi, qr, qi, th);
-    return y;
-}
-
 // [alpha]_pi of alpha = a + b - c - d: wrapped into (-pi, pi] by
 // alpha + 2 pi floor((pi - alpha)/(2 pi)).
 static __device__ __noinline__ double wrap_plaq_fp64(float a, float b, float c, float d)
@@ -51,37 +39,56 @@ static __device__ __noinline__ double wrap_plaq_fp64(float a, float b, float c, 
     return __dadd_rn(al, __dmul_rn(2.0 * kPiD, k));
 }
 
-static __device__ __forceinline__ float wrap_plaq(float a, float b, float c, float d)
+// atan2 to about 1.5e-3 rad: the rational arctangent approximation of Rajan, Wang,
+// Inkol & Joyal ("Efficient approximations for the arctangent function", IEEE
+// Signal Processing Magazine 23(3), 2006), atan(a) ~ (pi/4) a - a (a - 1)(0.2447 +
+// 0.0663 a) on [0, 1], extended by octant symmetry.  The winding count only needs
+// each link phase to well within pi/5 (the plaquette sum is an exact multiple of
+// 2 pi); which side of the branch cut a phase falls on is decided by the sign of
+// the imaginary part, handled by the callers.  Requires max(|y|, |x|) > 0.
+static __device__ __forceinline__ float atan2_coarse(float y, float x)
 {
-    float al = ((a + b) - c) - d;
-    float w = al + kTwoPiF * floorf((kPiF - al) * kInvTwoPiF);
-    float mag = fabsf(a) + fabsf(b) + fabsf(c) + fabsf(d);
-    if (fabsf(w) > kPiF - (kTie + 1e-6f * mag)) w = (float)wrap_plaq_fp64(a, b, c, d);
-    return w;
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float a = __fdividef(mn, mx);
+    float r = 0.785398163f * a - a * (a - 1.f) * (0.2447f + 0.0663f * a);
+    if (ay > ax) r = 1.570796327f - r;
+    if (x < 0.f) r = 3.141592654f - r;
+    return y < 0.f ? -r : r;
 }
 
+// true when the float32 complex number z = (zr, zi) is too close to the branch cut
+// of arg (the negative real axis, or z = 0) for its float32 sign to decide the branch
+static __device__ __forceinline__ bool near_cut(float zr, float zi)
+{
+    return (zr <= 0.f) && (fabsf(zi) <= kTie * fabsf(zr));
+}
 
 // Y_i(x) from a precomputed link phase V_i = (cos theta_i, sin theta_i) = conj(U_i);
-// the FP64 fallback recomputes from theta itself.
+// the FP64 fallback recomputes from theta_i, which the caller loads only then.
+template <class ThetaFn>
 static __device__ __forceinline__ float link_phase_v(float pr, float pi, float qr, float qi, float vc, float vs,
-                                                     float th)
+                                                     ThetaFn theta)
 {
     const float hr = vc * qr + vs * qi;   // U_i q with U_i = vc - i vs
     const float hi = vc * qi - vs * qr;
     const float zr = pr * hr + pi * hi;   // conj(p) U_i q
     const float zi = pr * hi - pi * hr;
-    float y = atan2f(zi, zr);
-    if (fabsf(y) > kPiF - kTie) y = (float)link_phase_fp64(pr, pi, qr, qi, th);
-    return y;
+    if (near_cut(zr, zi)) return (float)link_phase_fp64(pr, pi, qr, qi, theta());
+    return atan2_coarse(zi, zr);
 }
 
 // [alpha]_pi from the plaquette product Q = exp(i alpha) (Eq. 15 conjugated); the
 // FP64 fallback recomputes alpha = a + b - c - d from the four link angles.
-static __device__ __forceinline__ float wrap_from_q(float qr, float qi, float a, float b, float c, float d)
+template <class AnglesFn>
+static __device__ __forceinline__ float wrap_from_q(float qr, float qi, AnglesFn angles)
 {
-    float w = atan2f(qi, qr);
-    if (fabsf(w) > kPiF - kTie) w = (float)wrap_plaq_fp64(a, b, c, d);
-    return w;
+    if (near_cut(qr, qi)) {
+        float a, b, c, d;
+        angles(a, b, c, d);
+        return (float)wrap_plaq_fp64(a, b, c, d);
+    }
+    return atan2_coarse(qi, qr);
 }
 
 static __device__ __forceinline__ int winding(float y1, float y2, float y3, float y4, float aw)

@@ -34,6 +34,22 @@ __global__ void init_kernel(float *pr, float *pim, size_t V, uint64_t seed, doub
 }
 
 // ---------------------------------------------------------------- windings field
+// W_ij(x) for every plaquette, from the same link phases (V = (cos, sin) of each
+// link angle), plaquette products and branch handling as the fused measurement.
+__device__ __forceinline__ float2 vphase(float th)
+{
+    float s, c;
+    sincosf(th, &s, &c);
+    return make_float2(c, s);
+}
+
+__device__ __forceinline__ float2 plaq_q(float2 vi, float2 vj, float2 vjp, float2 vip)
+{
+    const float2 a = make_float2(vi.x * vj.x + vi.y * vj.y, vi.y * vj.x - vi.x * vj.y);
+    const float2 b = make_float2(vjp.x * vip.x + vjp.y * vip.y, vjp.y * vip.x - vjp.x * vip.y);
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
 __global__ void windings_kernel(const float *__restrict__ pr, const float *__restrict__ pim,
                                 const float *__restrict__ tx, const float *__restrict__ ty,
                                 const float *__restrict__ tz, int N, int8_t *W)
@@ -47,18 +63,29 @@ __global__ void windings_kernel(const float *__restrict__ pr, const float *__res
     const float p0r = pr[s], p0i = pim[s];
     const float pxr = pr[sxp], pxi = pim[sxp], pyr = pr[syp], pyi = pim[syp], pzr = pr[szp], pzi = pim[szp];
     const float tx0 = tx[s], ty0 = ty[s], tz0 = tz[s];
-    const float Yx = link_phase(p0r, p0i, pxr, pxi, tx0);
-    const float Yy = link_phase(p0r, p0i, pyr, pyi, ty0);
-    const float Yz = link_phase(p0r, p0i, pzr, pzi, tz0);
-    const float Yy_x = link_phase(pxr, pxi, pr[sxy], pim[sxy], ty[sxp]);
-    const float Yz_x = link_phase(pxr, pxi, pr[sxz], pim[sxz], tz[sxp]);
-    const float Yx_y = link_phase(pyr, pyi, pr[sxy], pim[sxy], tx[syp]);
-    const float Yz_y = link_phase(pyr, pyi, pr[syz], pim[syz], tz[syp]);
-    const float Yx_z = link_phase(pzr, pzi, pr[sxz], pim[sxz], tx[szp]);
-    const float Yy_z = link_phase(pzr, pzi, pr[syz], pim[syz], ty[szp]);
-    W[s] = (int8_t)winding(Yx, Yy_x, Yx_y, Yy, wrap_plaq(tx0, ty[sxp], tx[syp], ty0));
-    W[V + s] = (int8_t)winding(Yx, Yz_x, Yx_z, Yz, wrap_plaq(tx0, tz[sxp], tx[szp], tz0));
-    W[2 * V + s] = (int8_t)winding(Yy, Yz_y, Yy_z, Yz, wrap_plaq(ty0, tz[syp], ty[szp], tz0));
+    const float tyx = ty[sxp], tzx = tz[sxp], txy = tx[syp], tzy = tz[syp], txz = tx[szp], tyz = ty[szp];
+    const float2 vx0 = vphase(tx0), vy0 = vphase(ty0), vz0 = vphase(tz0);
+    const float2 vyx = vphase(tyx), vzx = vphase(tzx), vxy = vphase(txy), vzy = vphase(tzy), vxz = vphase(txz),
+                 vyz = vphase(tyz);
+    auto Y = [](float ar, float ai, float br, float bi, float2 v, float th) {
+        return link_phase_v(ar, ai, br, bi, v.x, v.y, [&] { return th; });
+    };
+    const float Yx = Y(p0r, p0i, pxr, pxi, vx0, tx0);
+    const float Yy = Y(p0r, p0i, pyr, pyi, vy0, ty0);
+    const float Yz = Y(p0r, p0i, pzr, pzi, vz0, tz0);
+    const float Yy_x = Y(pxr, pxi, pr[sxy], pim[sxy], vyx, tyx);
+    const float Yz_x = Y(pxr, pxi, pr[sxz], pim[sxz], vzx, tzx);
+    const float Yx_y = Y(pyr, pyi, pr[sxy], pim[sxy], vxy, txy);
+    const float Yz_y = Y(pyr, pyi, pr[syz], pim[syz], vzy, tzy);
+    const float Yx_z = Y(pzr, pzi, pr[sxz], pim[sxz], vxz, txz);
+    const float Yy_z = Y(pzr, pzi, pr[syz], pim[syz], vyz, tyz);
+    const float2 Qxy = plaq_q(vx0, vy0, vyx, vxy), Qxz = plaq_q(vx0, vz0, vzx, vxz), Qyz = plaq_q(vy0, vz0, vzy, vyz);
+    const float wxy = wrap_from_q(Qxy.x, Qxy.y, [&](float &a, float &b, float &c, float &d) { a = tx0; b = tyx; c = txy; d = ty0; });
+    const float wxz = wrap_from_q(Qxz.x, Qxz.y, [&](float &a, float &b, float &c, float &d) { a = tx0; b = tzx; c = txz; d = tz0; });
+    const float wyz = wrap_from_q(Qyz.x, Qyz.y, [&](float &a, float &b, float &c, float &d) { a = ty0; b = tzy; c = tyz; d = tz0; });
+    W[s] = (int8_t)winding(Yx, Yy_x, Yx_y, Yy, wxy);
+    W[V + s] = (int8_t)winding(Yx, Yz_x, Yx_z, Yz, wxz);
+    W[2 * V + s] = (int8_t)winding(Yy, Yz_y, Yy_z, Yz, wyz);
 }
 
 // ---------------------------------------------------------------- box gather

@@ -5,11 +5,11 @@
 // planes.  For every plane it
 //   A  turns the link angles of plane z+1 into link phases V_i = (cos th_i, sin th_i)
 //      (one sincos per link, Eq. 13) and stages them with phi in shared memory,
-//      over the tile plus a one-site ring (the halo);
+//      over the tile plus a one-site ring;
 //   B  forms the plaquettes of plane z as products of four link phases
 //      (Eq. 15: Q_ij = V_i(x) V_j(x+i) V_i(x+j)^* V_j(x)^* = exp(i alpha_ij)),
-//      so sin alpha_ij = Im Q_ij and cos alpha_ij = Re Q_ij, for the tile and its
-//      backward ring;
+//      so sin alpha_ij = Im Q_ij and cos alpha_ij = Re Q_ij, for the tile and the
+//      backward ring (row -1 needs xy and yz, column -1 needs xy and xz);
 //   C  kicks Pi (covariant Laplacian, Eq. 14, minus the potential) and E
 //      (lattice curl of sin alpha plus the current Im[phi^* U phi(x+i)]) with the
 //      Crank-Nicolson damping of Eqs. 7-8, drifts phi and theta (Eqs. 9-10), and
@@ -19,6 +19,7 @@
 // carried in registers from the previous plane; in-plane neighbours come from
 // shared memory.  Every link phase and plaquette of the tile is computed once.
 // Tile coordinates wrap modulo N, so ragged tiles and N < 32 need no special path.
+// Site offsets are 32-bit (the handle limits N^3 below 2^32).
 #include "ahs_device.cuh"
 
 #include <cstddef>
@@ -37,7 +38,7 @@ struct Tile {
     static_assert(NHA <= NT && NHB <= NT, "ring items must fit one pass of the CTA");
 
     struct Plane {
-        float vxc[NR], vxs[NR], vyc[NR], vys[NR], vzc[NR], vzs[NR], pr[NR], pi[NR];
+        float2 vx[NR], vy[NR], vz[NR], ph[NR];
     };
     struct Smem {
         Plane pl[2];
@@ -68,7 +69,7 @@ __device__ __forceinline__ int wrapN(int v, int N)
     return v < 0 ? v + N : v;
 }
 
-__device__ __forceinline__ Raw load_raw(const StepPtrs &P, size_t o)
+__device__ __forceinline__ Raw load_raw(const StepPtrs &P, uint32_t o)
 {
     Raw a;
     a.tx = __ldg(P.tx + o);
@@ -79,7 +80,7 @@ __device__ __forceinline__ Raw load_raw(const StepPtrs &P, size_t o)
     return a;
 }
 
-__device__ __forceinline__ PE load_pe(const StepPtrs &P, size_t o)
+__device__ __forceinline__ PE load_pe(const StepPtrs &P, uint32_t o)
 {
     PE a;
     a.qr = __ldg(P.qr + o);
@@ -90,38 +91,23 @@ __device__ __forceinline__ PE load_pe(const StepPtrs &P, size_t o)
     return a;
 }
 
-// complex helpers: (a) * (b), (a) * conj(b)
-__device__ __forceinline__ void cmul(float ar, float ai, float br, float bi, float &cr, float &ci)
+// complex helpers: a * b and a * conj(b)
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
-    cr = ar * br - ai * bi;
-    ci = ar * bi + ai * br;
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ void cmulc(float ar, float ai, float br, float bi, float &cr, float &ci)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
 {
-    cr = ar * br + ai * bi;
-    ci = ai * br - ar * bi;
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
 // Q = V_i(x) conj(V_j(x)) * V_j(x+i) conj(V_i(x+j))
-__device__ __forceinline__ void plaquette(float ic, float is, float jc, float js, float jpc, float jps, float ipc,
-                                          float ips, float &qr, float &qi)
+__device__ __forceinline__ float2 plaquette(float2 vi, float2 vj, float2 vjp, float2 vip)
 {
-    float ar, ai, br, bi;
-    cmulc(ic, is, jc, js, ar, ai);
-    cmulc(jpc, jps, ipc, ips, br, bi);
-    cmul(ar, ai, br, bi, qr, qi);
+    return cmul(cmulc(vi, vj), cmulc(vjp, vip));
 }
 
-struct KSum {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v)
-    {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-};
+__device__ __forceinline__ int next_plane(int z, int N) { return z + 1 == N ? 0 : z + 1; }
 
 template <int BY, bool MEASURE, bool STORE>
 __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, int N, int Dz, double *partials)
@@ -133,11 +119,11 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
     const int tx = threadIdx.x, ty = threadIdx.y, t = tx + 32 * ty;
     const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
     const int zend = min(z0 + Dz, N);
-    const size_t NN = (size_t)N * N;
+    const uint32_t NN = (uint32_t)N * (uint32_t)N;
 
-    // core item: this thread's own site; ring items of phase A and B
+    // core item: this thread's own site; ring items of phases A and B
     const int cx = wrapN(x0 + tx, N), cy = wrapN(y0 + ty, N);
-    const int coff = cx + N * cy;
+    const uint32_t coff = (uint32_t)cx + (uint32_t)N * (uint32_t)cy;
     const bool valid = (x0 + tx < N) && (y0 + ty < N);
     int hax = 0, hay = 0;
     const bool hasA = t < T::NHA;
@@ -147,161 +133,161 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
         else if (t < 2 * T::RX + BY) { hax = -1; hay = t - 2 * T::RX; }
         else { hax = T::BX; hay = t - 2 * T::RX - BY; }
     }
-    const int haoff = wrapN(x0 + hax, N) + N * wrapN(y0 + hay, N);
-    int hbx = 0, hby = 0;
+    const uint32_t haoff = (uint32_t)wrapN(x0 + hax, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hay, N);
     const bool hasB = t < T::NHB;
-    if (hasB) {
-        if (t < T::BX) { hbx = t; hby = -1; }
-        else { hbx = -1; hby = t - T::BX; }
-    }
-    // measurement: forward ring of the link phases Y (row BY for Y_x/Y_z, column BX for Y_y/Y_z)
-    int hyx = 0, hyy = 0;
+    const bool ringRow = t < T::BX;                  // phase B ring: row -1 (else column -1)
+    const int hbx = ringRow ? t : -1, hby = ringRow ? -1 : t - T::BX;
+    // measurement rings: forward link phases (row BY for Y_x/Y_z, column BX for Y_y/Y_z)
+    // and the old E of the backward ring for the Gauss residual
+    const int hyx = ringRow ? t : T::BX, hyy = ringRow ? BY : t - T::BX;
+    uint32_t hyoff = 0, hboff = 0;
     if (MEASURE && hasB) {
-        if (t < T::BX) { hyx = t; hyy = BY; }
-        else { hyx = T::BX; hyy = t - T::BX; }
+        hyoff = (uint32_t)wrapN(x0 + hyx, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hyy, N);
+        hboff = (uint32_t)wrapN(x0 + hbx, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hby, N);
     }
+    const uint32_t cxpoff = (uint32_t)wrapN(cx + 1, N) + (uint32_t)N * (uint32_t)cy;
+    const uint32_t cypoff = (uint32_t)cx + (uint32_t)N * (uint32_t)wrapN(cy + 1, N);
 
-    auto zoff = [&](int z) { return (size_t)wrapN(z, N) * NN; };
-
-    // phase A for one item into plane buffer b
     auto phaseA = [&](const Raw &a, int ri, typename T::Plane &pl) {
         float s, c;
         sincosf(a.tx, &s, &c);
-        pl.vxc[ri] = c; pl.vxs[ri] = s;
+        pl.vx[ri] = make_float2(c, s);
         sincosf(a.ty, &s, &c);
-        pl.vyc[ri] = c; pl.vys[ri] = s;
+        pl.vy[ri] = make_float2(c, s);
         sincosf(a.tz, &s, &c);
-        pl.vzc[ri] = c; pl.vzs[ri] = s;
-        pl.pr[ri] = a.pr;
-        pl.pi[ri] = a.pi;
+        pl.vz[ri] = make_float2(c, s);
+        pl.ph[ri] = make_float2(a.pr, a.pi);
     };
 
-    // phase B for one site (ex, ey) of plane buffer b0 with the next plane b1
-    auto phaseB = [&](int ex, int ey, const typename T::Plane &p0, const typename T::Plane &p1, float &qxyr,
-                      float &qxyi, float &qxzr, float &qxzi, float &qyzr, float &qyzi) {
-        const int r0 = T::r(ex, ey), rxp = T::r(ex + 1, ey), ryp = T::r(ex, ey + 1);
-        const float vxc = p0.vxc[r0], vxs = p0.vxs[r0], vyc = p0.vyc[r0], vys = p0.vys[r0];
-        const float vzc = p0.vzc[r0], vzs = p0.vzs[r0];
-        plaquette(vxc, vxs, vyc, vys, p0.vyc[rxp], p0.vys[rxp], p0.vxc[ryp], p0.vxs[ryp], qxyr, qxyi);
-        plaquette(vxc, vxs, vzc, vzs, p0.vzc[rxp], p0.vzs[rxp], p1.vxc[r0], p1.vxs[r0], qxzr, qxzi);
-        plaquette(vyc, vys, vzc, vzs, p0.vzc[ryp], p0.vzs[ryp], p1.vyc[r0], p1.vys[r0], qyzr, qyzi);
-    };
+    // plane indices (wrapped) of zz, zz+1, zz+2, maintained incrementally
+    int zc = wrapN(z0 - 1, N);
+    int z1 = next_plane(zc, N);
+    int z2 = next_plane(z1, N);
 
     // ---------------------------------------------------------------- prologue
-    Raw rc = load_raw(P, zoff(z0 - 1) + coff);
-    Raw rh = hasA ? load_raw(P, zoff(z0 - 1) + haoff) : Raw{};
+    Raw rc = load_raw(P, (uint32_t)zc * NN + coff);
+    Raw rh = hasA ? load_raw(P, (uint32_t)zc * NN + haoff) : Raw{};
     phaseA(rc, T::r(tx, ty), S.pl[0]);
     if (hasA) phaseA(rh, T::r(hax, hay), S.pl[0]);
-    float thx = rc.tx, thy = rc.ty, thz = rc.tz;   // own theta of the current plane
-    rc = load_raw(P, zoff(z0) + coff);
-    if (hasA) rh = load_raw(P, zoff(z0) + haoff);
+    float thx = rc.tx, thy = rc.ty, thz = rc.tz;   // own theta of plane zz
+    rc = load_raw(P, (uint32_t)z1 * NN + coff);
+    if (hasA) rh = load_raw(P, (uint32_t)z1 * NN + haoff);
     PE pe_next{}, pe_cur{};
     float ezPrev = 0.f;
-    if (MEASURE) ezPrev = __ldg(P.ez + zoff(z0 - 1) + coff);
+    if (MEASURE) ezPrev = __ldg(P.ez + (uint32_t)zc * NN + coff);
 
-    // carried from plane z-1 (own column)
-    float phPrevR = 0.f, phPrevI = 0.f, vzPrevC = 1.f, vzPrevS = 0.f, sxzPrev = 0.f, syzPrev = 0.f;
+    // carried from plane zz-1 (own column)
+    float2 phPrev = make_float2(0.f, 0.f), vzPrev = make_float2(1.f, 0.f);
+    float sxzPrev = 0.f, syzPrev = 0.f;
+    float YxCar = 0.f, YyCar = 0.f;   // Y_x, Y_y of plane zz (measurement)
 
     Acc acc;
-    KSum ks[NSUM];
     if (MEASURE) acc_zero(acc);
 
     int b = 0;   // plane buffer holding plane zz
     for (int zz = z0 - 1; zz < zend; ++zz) {
         typename T::Plane &pc = S.pl[b];
         typename T::Plane &pn = S.pl[b ^ 1];
+        const uint32_t oc = (uint32_t)zc * NN, o1 = (uint32_t)z1 * NN, o2 = (uint32_t)z2 * NN;
         // ---- A: link phases and phi of plane zz+1
         phaseA(rc, T::r(tx, ty), pn);
         if (hasA) phaseA(rh, T::r(hax, hay), pn);
         const float nthx = rc.tx, nthy = rc.ty, nthz = rc.tz;
         if (zz + 2 <= zend) {
-            rc = load_raw(P, zoff(zz + 2) + coff);
-            if (hasA) rh = load_raw(P, zoff(zz + 2) + haoff);
+            rc = load_raw(P, o2 + coff);
+            if (hasA) rh = load_raw(P, o2 + haoff);
         }
         pe_cur = pe_next;
-        if (zz + 1 < zend) pe_next = load_pe(P, zoff(zz + 1) + coff);
+        if (zz + 1 < zend) pe_next = load_pe(P, o1 + coff);
         __syncthreads();
 
         // ---- B: plaquettes of plane zz (tile + backward ring)
-        float qxyr, qxyi, qxzr, qxzi, qyzr, qyzi;
-        phaseB(tx, ty, pc, pn, qxyr, qxyi, qxzr, qxzi, qyzr, qyzi);
+        const int r0 = T::r(tx, ty), rxp = T::r(tx + 1, ty), ryp = T::r(tx, ty + 1);
+        const float2 vx0 = pc.vx[r0], vy0 = pc.vy[r0], vz0 = pc.vz[r0];
+        const float2 Qxy = plaquette(vx0, vy0, pc.vy[rxp], pc.vx[ryp]);
+        const float2 Qxz = plaquette(vx0, vz0, pc.vz[rxp], pn.vx[r0]);
+        const float2 Qyz = plaquette(vy0, vz0, pc.vz[ryp], pn.vy[r0]);
         {
             const int qi0 = T::q(tx, ty);
-            S.sxy[qi0] = qxyi;
-            S.sxz[qi0] = qxzi;
-            S.syz[qi0] = qyzi;
+            S.sxy[qi0] = Qxy.y;
+            S.sxz[qi0] = Qxz.y;
+            S.syz[qi0] = Qyz.y;
         }
         if (hasB) {
-            float a1, a2, a3, a4, a5, a6;
-            phaseB(hbx, hby, pc, pn, a1, a2, a3, a4, a5, a6);
+            const int rb = T::r(hbx, hby), rbx = T::r(hbx + 1, hby), rby = T::r(hbx, hby + 1);
+            const float2 bx = pc.vx[rb], by = pc.vy[rb], bz = pc.vz[rb];
             const int qh = T::q(hbx, hby);
-            S.sxy[qh] = a2;
-            S.sxz[qh] = a4;
-            S.syz[qh] = a6;
+            S.sxy[qh] = plaquette(bx, by, pc.vy[rbx], pc.vx[rby]).y;
+            if (ringRow) S.syz[qh] = plaquette(by, bz, pc.vz[rby], pn.vy[rb]).y;
+            else S.sxz[qh] = plaquette(bx, bz, pc.vz[rbx], pn.vx[rb]).y;
         }
         if (MEASURE && zz >= z0) {
-            // link phases Y_i of plane zz on the tile and its forward ring
-            const size_t zo = zoff(zz);
-            const int r0 = T::r(tx, ty), wi = T::w(tx, ty);
-            const float p0r = pc.pr[r0], p0i = pc.pi[r0];
-            S.yx[wi] = link_phase_v(p0r, p0i, pc.pr[T::r(tx + 1, ty)], pc.pi[T::r(tx + 1, ty)], pc.vxc[r0], pc.vxs[r0], thx);
-            S.yy[wi] = link_phase_v(p0r, p0i, pc.pr[T::r(tx, ty + 1)], pc.pi[T::r(tx, ty + 1)], pc.vyc[r0], pc.vys[r0], thy);
-            S.yz[wi] = link_phase_v(p0r, p0i, pn.pr[r0], pn.pi[r0], pc.vzc[r0], pc.vzs[r0], thz);
+            // link phases Y_i of plane zz on the tile (Y_x, Y_y carried from the
+            // previous plane) and on its forward ring; old E of the backward ring
+            const int wi = T::w(tx, ty);
+            const float2 p0 = pc.ph[r0], pz = pn.ph[r0];
+            S.yx[wi] = YxCar;
+            S.yy[wi] = YyCar;
+            const float tz0 = thz;
+            S.yz[wi] = link_phase_v(p0.x, p0.y, pz.x, pz.y, vz0.x, vz0.y, [&] { return tz0; });
             S.ex[T::q(tx, ty)] = pe_cur.ex;
             S.ey[T::q(tx, ty)] = pe_cur.ey;
             if (hasB) {
                 const int rh0 = T::r(hyx, hyy), wh = T::w(hyx, hyy);
-                const size_t ho = zo + wrapN(x0 + hyx, N) + (size_t)N * wrapN(y0 + hyy, N);
-                const float hr = pc.pr[rh0], hi = pc.pi[rh0];
-                if (t < T::BX) {   // row BY: Y_x and Y_z
-                    S.yx[wh] = link_phase_v(hr, hi, pc.pr[T::r(hyx + 1, hyy)], pc.pi[T::r(hyx + 1, hyy)], pc.vxc[rh0],
-                                            pc.vxs[rh0], __ldg(P.tx + ho));
-                } else {           // column BX: Y_y and Y_z
-                    S.yy[wh] = link_phase_v(hr, hi, pc.pr[T::r(hyx, hyy + 1)], pc.pi[T::r(hyx, hyy + 1)], pc.vyc[rh0],
-                                            pc.vys[rh0], __ldg(P.ty + ho));
+                const uint32_t ho = oc + hyoff;
+                const float2 hp = pc.ph[rh0];
+                if (ringRow) {   // row BY: Y_x
+                    const float2 q = pc.ph[T::r(hyx + 1, hyy)], v = pc.vx[rh0];
+                    S.yx[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return __ldg(P.tx + ho); });
+                } else {         // column BX: Y_y
+                    const float2 q = pc.ph[T::r(hyx, hyy + 1)], v = pc.vy[rh0];
+                    S.yy[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return __ldg(P.ty + ho); });
                 }
-                S.yz[wh] = link_phase_v(hr, hi, pn.pr[rh0], pn.pi[rh0], pc.vzc[rh0], pc.vzs[rh0], __ldg(P.tz + ho));
-                // old E of the backward ring for the Gauss residual
-                const size_t eo = zo + wrapN(x0 + hbx, N) + (size_t)N * wrapN(y0 + hby, N);
-                if (t < T::BX) S.ey[T::q(hbx, hby)] = __ldg(P.ey + eo);
-                else S.ex[T::q(hbx, hby)] = __ldg(P.ex + eo);
+                const float2 q = pn.ph[rh0], v = pc.vz[rh0];
+                S.yz[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return __ldg(P.tz + ho); });
+                if (ringRow) S.ey[T::q(hbx, hby)] = __ldg(P.ey + oc + hboff);
+                else S.ex[T::q(hbx, hby)] = __ldg(P.ex + oc + hboff);
             }
         }
         __syncthreads();
 
+        // measurement: link phases Y_x, Y_y of plane zz+1 on every column of the tile
+        // (ragged-tile columns too: they are the periodic images the ring reads)
+        float YxNext = 0.f, YyNext = 0.f;
+        if (MEASURE) {
+            const float2 pn0 = pn.ph[r0], vxn = pn.vx[r0], vyn = pn.vy[r0];
+            const float2 qxn = pn.ph[rxp], qyn = pn.ph[ryp];
+            const float tnx = nthx, tny = nthy;
+            YxNext = link_phase_v(pn0.x, pn0.y, qxn.x, qxn.y, vxn.x, vxn.y, [&] { return tnx; });
+            YyNext = link_phase_v(pn0.x, pn0.y, qyn.x, qyn.y, vyn.x, vyn.y, [&] { return tny; });
+        }
+
         // ---- C: kick and drift of plane zz
-        const int r0 = T::r(tx, ty);
-        const float p0r = pc.pr[r0], p0i = pc.pi[r0];
-        const float vzc = pc.vzc[r0], vzs = pc.vzs[r0];
+        const float2 p0 = pc.ph[r0];
         if (zz >= z0 && valid) {
-            const float vxc = pc.vxc[r0], vxs = pc.vxs[r0], vyc = pc.vyc[r0], vys = pc.vys[r0];
-            const int rxm = T::r(tx - 1, ty), rxp = T::r(tx + 1, ty), rym = T::r(tx, ty - 1), ryp = T::r(tx, ty + 1);
+            const int rxm = T::r(tx - 1, ty), rym = T::r(tx, ty - 1);
             // forward hops U_i(x) phi(x+i) = conj(V_i) phi(x+i)
-            float hxr, hxi, hyr, hyi, hzr, hzi;
-            cmulc(pc.pr[rxp], pc.pi[rxp], vxc, vxs, hxr, hxi);
-            cmulc(pc.pr[ryp], pc.pi[ryp], vyc, vys, hyr, hyi);
-            cmulc(pn.pr[r0], pn.pi[r0], vzc, vzs, hzr, hzi);
+            const float2 hx = cmulc(pc.ph[rxp], vx0);
+            const float2 hy = cmulc(pc.ph[ryp], vy0);
+            const float2 hz = cmulc(pn.ph[r0], vz0);
             // backward hops U_i(x-i)^* phi(x-i) = V_i(x-i) phi(x-i)
-            float bxr, bxi, byr, byi, bzr, bzi;
-            cmul(pc.vxc[rxm], pc.vxs[rxm], pc.pr[rxm], pc.pi[rxm], bxr, bxi);
-            cmul(pc.vyc[rym], pc.vys[rym], pc.pr[rym], pc.pi[rym], byr, byi);
-            cmul(vzPrevC, vzPrevS, phPrevR, phPrevI, bzr, bzi);
-            const float hsr = ((hxr + bxr) + (hyr + byr)) + (hzr + bzr);
-            const float hsi = ((hxi + bxi) + (hyi + byi)) + (hzi + bzi);
-            const float mod2 = p0r * p0r + p0i * p0i;
+            const float2 bxh = cmul(pc.vx[rxm], pc.ph[rxm]);
+            const float2 byh = cmul(pc.vy[rym], pc.ph[rym]);
+            const float2 bzh = cmul(vzPrev, phPrev);
+            const float hsr = ((hx.x + bxh.x) + (hy.x + byh.x)) + (hz.x + bzh.x);
+            const float hsi = ((hx.y + bxh.y) + (hy.y + byh.y)) + (hz.y + bzh.y);
+            const float mod2 = p0.x * p0.x + p0.y * p0.y;
             const float potf = k.kpi_pot * (mod2 - k.sigma2);
-            const float qnr = k.cpi * pe_cur.qr + k.kpi_lap * (hsr - 6.f * p0r) - potf * p0r;
-            const float qni = k.cpi * pe_cur.qi + k.kpi_lap * (hsi - 6.f * p0i) - potf * p0i;
+            const float qnr = k.cpi * pe_cur.qr + k.kpi_lap * (hsr - 6.f * p0.x) - potf * p0.x;
+            const float qni = k.cpi * pe_cur.qi + k.kpi_lap * (hsi - 6.f * p0.y) - potf * p0.y;
             // currents J_i = Im(conj(phi) U_i phi(x+i))
-            const float jx = p0r * hxi - p0i * hxr;
-            const float jy = p0r * hyi - p0i * hyr;
-            const float jz = p0r * hzi - p0i * hzr;
-            const int qi0 = T::q(tx, ty);
-            const float sxy = qxyi, sxz = qxzi, syz = qyzi;
+            const float jx = p0.x * hx.y - p0.y * hx.x;
+            const float jy = p0.x * hy.y - p0.y * hy.x;
+            const float jz = p0.x * hz.y - p0.y * hz.x;
+            const float sxy = Qxy.y, sxz = Qxz.y, syz = Qyz.y;
             const float cxv = -(sxy - S.sxy[T::q(tx, ty - 1)]) - (sxz - sxzPrev);
             const float cyv = (sxy - S.sxy[T::q(tx - 1, ty)]) - (syz - syzPrev);
             const float czv = (sxz - S.sxz[T::q(tx - 1, ty)]) + (syz - S.syz[T::q(tx, ty - 1)]);
-            (void)qi0;
             const float enx = k.ce * pe_cur.ex + k.ke_curl * cxv + k.ke_cur * jx;
             const float eny = k.ce * pe_cur.ey + k.ke_curl * cyv + k.ke_cur * jy;
             const float enz = k.ce * pe_cur.ez + k.ke_curl * czv + k.ke_cur * jz;
@@ -309,57 +295,52 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
             if (MEASURE) {
                 const float pbr = 0.5f * (pe_cur.qr + qnr), pbi = 0.5f * (pe_cur.qi + qni);
                 const float K = pbr * pbr + pbi * pbi;
-                const float gxr = hxr - p0r, gxi = hxi - p0i, gyr = hyr - p0r, gyi = hyi - p0i;
-                const float gzr = hzr - p0r, gzi = hzi - p0i;
+                const float gxr = hx.x - p0.x, gxi = hx.y - p0.y, gyr = hy.x - p0.x, gyi = hy.y - p0.y;
+                const float gzr = hz.x - p0.x, gzi = hz.y - p0.y;
                 const float G = k.m_grad * ((gxr * gxr + gxi * gxi) + (gyr * gyr + gyi * gyi) + (gzr * gzr + gzi * gzi));
                 const float dm = mod2 - k.sigma2;
                 const float V = k.m_pot * dm * dm;
                 const float ebx = 0.5f * (pe_cur.ex + enx), eby = 0.5f * (pe_cur.ey + eny), ebz = 0.5f * (pe_cur.ez + enz);
                 const float El = k.m_el * (ebx * ebx + eby * eby + ebz * ebz);
-                const float B = k.m_mag * ((1.f - qxyr) + (1.f - qxzr) + (1.f - qyzr));
+                const float B = k.m_mag * ((1.f - Qxy.x) + (1.f - Qxz.x) + (1.f - Qyz.x));
                 const float L = K - G - V + El - B;
                 const float rho = K + G + V + El + B;
                 const float pres = K - G * (1.f / 3.f) - V + (El + B) * (1.f / 3.f);
                 const float div = ((pe_cur.ex - S.ex[T::q(tx - 1, ty)]) + (pe_cur.ey - S.ey[T::q(tx, ty - 1)]) +
                                    (pe_cur.ez - ezPrev)) * k.inv_dx;
-                const float g = div - k.m_gauss * (p0r * pe_cur.qi - p0i * pe_cur.qr);
-                ks[Q_K].add(K); ks[Q_G].add(G); ks[Q_V].add(V); ks[Q_EL].add(El); ks[Q_B].add(B);
-                ks[Q_L].add(L); ks[Q_KL].add(K * L); ks[Q_GL].add(G * L); ks[Q_PL].add(pres * L);
-                ks[Q_RL].add(rho * L); ks[Q_G2].add(g * g);
+                const float g = div - k.m_gauss * (p0.x * pe_cur.qi - p0.y * pe_cur.qr);
+                acc.s[Q_K] += K; acc.s[Q_G] += G; acc.s[Q_V] += V; acc.s[Q_EL] += El; acc.s[Q_B] += B;
+                acc.s[Q_L] += L; acc.s[Q_KL] += K * L; acc.s[Q_GL] += G * L; acc.s[Q_PL] += pres * L;
+                acc.s[Q_RL] += rho * L; acc.s[Q_G2] += g * g;
                 acc.gmax = fmaxf(acc.gmax, fabsf(g));
                 if (!isfinite(rho) || !isfinite(L) || !isfinite(g)) acc.nf += 1;
 
                 // plaquette windings with lower corner x
                 const int wi = T::w(tx, ty);
-                const float Yx = S.yx[wi], Yy = S.yy[wi], Yz = S.yz[wi];
-                const size_t o = zoff(zz) + coff;
-                const size_t oxp = zoff(zz) + wrapN(cx + 1, N) + (size_t)N * cy;
-                const size_t oyp = zoff(zz) + cx + (size_t)N * wrapN(cy + 1, N);
-                const size_t ozp = zoff(zz + 1) + coff;
-                // Y_x, Y_y of plane zz+1 (own column)
-                const int rxpn = T::r(tx + 1, ty), rypn = T::r(tx, ty + 1);
-                const float Yxn = link_phase_v(pn.pr[r0], pn.pi[r0], pn.pr[rxpn], pn.pi[rxpn], pn.vxc[r0], pn.vxs[r0], nthx);
-                const float Yyn = link_phase_v(pn.pr[r0], pn.pi[r0], pn.pr[rypn], pn.pi[rypn], pn.vyc[r0], pn.vys[r0], nthy);
-                (void)o;
-                const float wxy = wrap_from_q(qxyr, qxyi, thx, __ldg(P.ty + oxp), __ldg(P.tx + oyp), thy);
-                const float wxz = wrap_from_q(qxzr, qxzi, thx, __ldg(P.tz + oxp), nthx, thz);
-                const float wyz = wrap_from_q(qyzr, qyzi, thy, __ldg(P.tz + oyp), nthy, thz);
+                const float Yx = YxCar, Yy = YyCar, Yz = S.yz[wi];
+                const float tnx = nthx, tny = nthy;
+                const float t0x = thx, t0y = thy, t0z = thz;
+                const float wxy = wrap_from_q(Qxy.x, Qxy.y, [&](float &a, float &bb, float &c, float &d) {
+                    a = t0x; bb = __ldg(P.ty + oc + cxpoff); c = __ldg(P.tx + oc + cypoff); d = t0y; });
+                const float wxz = wrap_from_q(Qxz.x, Qxz.y, [&](float &a, float &bb, float &c, float &d) {
+                    a = t0x; bb = __ldg(P.tz + oc + cxpoff); c = tnx; d = t0z; });
+                const float wyz = wrap_from_q(Qyz.x, Qyz.y, [&](float &a, float &bb, float &c, float &d) {
+                    a = t0y; bb = __ldg(P.tz + oc + cypoff); c = tny; d = t0z; });
                 const int nxy = winding(Yx, S.yy[T::w(tx + 1, ty)], S.yx[T::w(tx, ty + 1)], Yy, wxy);
-                const int nxz = winding(Yx, S.yz[T::w(tx + 1, ty)], Yxn, Yz, wxz);
-                const int nyz = winding(Yy, S.yz[T::w(tx, ty + 1)], Yyn, Yz, wyz);
+                const int nxz = winding(Yx, S.yz[T::w(tx + 1, ty)], YxNext, Yz, wxz);
+                const int nyz = winding(Yy, S.yz[T::w(tx, ty + 1)], YyNext, Yz, wyz);
                 acc.wind += abs(nxy) + abs(nxz) + abs(nyz);
-                (void)ozp;
             }
 
             if (STORE) {
-                const size_t o = zoff(zz) + coff;
+                const uint32_t o = oc + coff;
                 P.qr1[o] = qnr;
                 P.qi1[o] = qni;
                 P.ex1[o] = enx;
                 P.ey1[o] = eny;
                 P.ez1[o] = enz;
-                P.pr1[o] = p0r + k.dphi * qnr;
-                P.pim1[o] = p0i + k.dphi * qni;
+                P.pr1[o] = p0.x + k.dphi * qnr;
+                P.pim1[o] = p0.y + k.dphi * qni;
                 float t1x = thx + k.dtheta * enx, t1y = thy + k.dtheta * eny, t1z = thz + k.dtheta * enz;
                 if (k.wrap) {
                     t1x += kTwoPiF * floorf((kPiF - t1x) * kInvTwoPiF);
@@ -372,18 +353,20 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
             }
         }
         // carry plane zz's own-column values to plane zz+1
-        phPrevR = p0r; phPrevI = p0i;
-        vzPrevC = vzc; vzPrevS = vzs;
-        sxzPrev = qxzi; syzPrev = qyzi;
+        phPrev = p0;
+        vzPrev = vz0;
+        sxzPrev = Qxz.y;
+        syzPrev = Qyz.y;
         if (MEASURE && zz >= z0) ezPrev = pe_cur.ez;
+        YxCar = YxNext;
+        YyCar = YyNext;
         thx = nthx; thy = nthy; thz = nthz;
+        zc = z1; z1 = z2; z2 = next_plane(z2, N);
         b ^= 1;
         __syncthreads();
     }
 
     if (MEASURE) {
-#pragma unroll
-        for (int qq = 0; qq < NSUM; ++qq) acc.s[qq] = ks[qq].s;
         const size_t bi = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
         block_reduce_store<32 * BY>(acc, partials + bi * NQ);
     }
