@@ -172,6 +172,34 @@ int ahs_kernel_time(ahs_t *h, int kind, double *ms_total, int64_t *launches, int
 /* ahs_device_bytes -- device memory held by the handle. */
 int ahs_device_bytes(ahs_t *h, size_t *bytes);
 
+/* ahs_measure_noalloc -- the measurement of ahs_measure on fields the caller
+ * owns, without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, because all of their
+ * device memory belongs to another allocator (a framework's caching allocator, or
+ * a pool reserved for the job up front) and a side allocation would fail,
+ * fragment that pool or stall on the allocator's device-wide synchronisation.
+ *   fields: device pointer to the ten float32 planes of AHS_FIELD_ALL (phi and
+ *           theta at the integer time `step`, Pi and E at step - 1/2), N^3 each,
+ *           site index x + N*(y + N*z); read only.
+ *   out:    device pointer to one ahs_obs_t, written by the call.
+ *   N, dx, dt, lambda0, e0, sigma, s, era: as for ahs_create; alpha and tau0 as
+ *           the AHS_OPT_ALPHA / AHS_OPT_TAU0 options.
+ *   stream: cudaStream_t (as void*) to run on; NULL for the legacy default stream.
+ * The call only enqueues work: synchronise the stream before reading *out.  Its
+ * scratch is a static device array of AHS_NOALLOC_MAX_ROWS rows of FP64 partial
+ * sums (2 MiB) that every GPU loading this library holds until the process
+ * exits; every CTA overwrites its own row, so nothing carries over between calls,
+ * but calls that overlap on the GPU (other streams, other threads) share the
+ * array and race.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Returns AHS_EINVAL for N outside [4, 1600] (a
+ * lattice whose CTAs cannot fit the scratch is rejected the same way), bad
+ * parameters or NULL buffers, AHS_ECUDA if a launch fails. */
+#define AHS_NOALLOC_MAX_ROWS 16384
+int ahs_measure_noalloc(int N, double dx, double dt, double lambda0, double e0, double sigma, double s,
+                        int era, double alpha, double tau0, int64_t step, const float *fields,
+                        ahs_obs_t *out, void *stream);
+
 void ahs_destroy(ahs_t *h);
 
 int ahs_last_error(void);

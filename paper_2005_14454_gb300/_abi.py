@@ -27,7 +27,7 @@ EXPORTS = (
     "ahs_create", "ahs_init", "ahs_step", "ahs_measure", "ahs_records", "ahs_fields",
     "ahs_set_fields", "ahs_fields_box", "ahs_windings", "ahs_set_option", "ahs_get_option",
     "ahs_set_stream", "ahs_kernel_time", "ahs_device_bytes", "ahs_destroy", "ahs_last_error",
-    "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs",
+    "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs", "ahs_measure_noalloc",
 )
 
 
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ahs_strerror.argtypes = [i]
     L.ahs_strerror.restype = ctypes.c_char_p
     L.ahs_sizeof_obs.restype = sz
+    L.ahs_measure_noalloc.argtypes = [i, d, d, d, d, d, d, i, d, d, ctypes.c_int64, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("ahs_create", "ahs_destroy", "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs"):
             getattr(L, name).restype = i

@@ -47,6 +47,12 @@ constexpr int kFields = 10;   // Re phi, Im phi, Re Pi, Im Pi, theta_xyz, E_xyz
 
 }  // namespace
 
+namespace eng {
+// error reporting for entry points defined in other translation units
+int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
+int report_ok() { return ok(); }
+}  // namespace eng
+
 struct ahs {
     int N = 0;
     size_t V = 0;

@@ -77,4 +77,8 @@ cudaError_t launch_windings(const float *pr, const float *pim, const float *tx, 
 cudaError_t launch_gather_box(const float *const *planes, int nplanes, int N, int x0, int y0, int z0,
                               int nx, int ny, int nz, float *dst, cudaStream_t st);
 
+// error state of the C ABI (ahs_last_error / ahs_last_error_message)
+int report_error(int code, const char *msg);
+int report_ok();
+
 }  // namespace eng
