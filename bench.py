@@ -104,12 +104,15 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- helpers
+STEP_KERNEL_SOURCES = ("ahs_step.cu", "ahs_device.cuh", "ahs_internal.cuh")
+
+
 def kernel_hash():
+    """Hash of the sources the step kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_14454_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP_KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
