@@ -159,6 +159,70 @@ def cpu_baseline(seconds=12.0, N=128):
             "sample": f"FP64 oracle, {N}^3 lattice of the same workload, {steps} leapfrog steps in {dt:.1f} s"}
 
 
+# --------------------------------------------------------------------- ensemble
+ENSEMBLE = [(128, 24), (192, 16), (256, 8)]     # (side, realisations), half radiation / half matter
+
+
+def ensemble_members():
+    members, seed = [], 1
+    for N, count in ENSEMBLE:
+        for j in range(count):
+            members.append((N, 1 if j % 2 == 0 else 2, seed))
+            seed += 1
+    return members
+
+
+def run_ensemble(torch):
+    """Realisations/hour of the ensemble 24x128^3 + 16x192^3 + 8x256^3 (s = 0, half
+    radiation, half matter, each evolved to half light-crossing with a measurement
+    every 10 steps): one batch (persistent launch per step, graph-replayed
+    measurement periods, autotuned z-chunks) against the same realisations run back
+    to back as single lattices.  Both time the evolution on the device (CUDA events);
+    the fields of the two runs are identical (same kernel, same coefficients)."""
+    from paper_2005_14454_gb300 import Batch, Lattice, _abi
+    members = ensemble_members()
+    N, era, seed = zip(*members)
+    sites = sum(n ** 3 * round((0.5 * PARAMS["dx"] * n - 1.0) / PARAMS["dt"]) for n in N)
+    with Batch(N, era, seed, measure_every=PERIOD, **PARAMS) as b:
+        b.init()
+        b.autotune()
+        _abi.ahs_batch_set_option(b.b, _abi.AHS_OPT_PROFILE, 1)
+        _abi.ahs_batch_kernel_time(b.b, reset=True)
+        t0 = time.perf_counter()
+        b.run()
+        wall_b = time.perf_counter() - t0
+        ms_b, steps_b = _abi.ahs_batch_kernel_time(b.b)
+        dz = sorted({(n, _abi.ahs_batch_member_zchunk(b.b, i)) for i, n in enumerate(N)})
+        by = int(_abi.ahs_batch_get_option(b.b, _abi.AHS_OPT_TILE_Y))
+    stream = torch.cuda.current_stream()
+    ms_s = 0.0
+    t0 = time.perf_counter()
+    for n, e, sd in members:
+        with Lattice(n, era=e, measure_every=PERIOD, stream=stream.cuda_stream, **PARAMS) as lat:
+            lat.init(sd)
+            steps = round((0.5 * PARAMS["dx"] * n - 1.0) / PARAMS["dt"])
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms_s += e0.elapsed_time(e1)
+    wall_s = time.perf_counter() - t0
+    R = len(members)
+    return {
+        "members": " + ".join(f"{c}x{n}^3" for n, c in ENSEMBLE) + ", half radiation / half matter, s=0, "
+                   f"to half light-crossing, measurement every {PERIOD} steps",
+        "batched_realisations_per_hour": R / (ms_b / 1e3) * 3600.0,
+        "back_to_back_realisations_per_hour": R / (ms_s / 1e3) * 3600.0,
+        "speedup": ms_s / ms_b,
+        "batched_site_updates_per_s": sites / (ms_b / 1e3),
+        "back_to_back_site_updates_per_s": sites / (ms_s / 1e3),
+        "batched_device_s": ms_b / 1e3, "back_to_back_device_s": ms_s / 1e3,
+        "batched_wall_s": wall_b, "back_to_back_wall_s_incl_init": wall_s,
+        "batch_tile_y": by, "batch_zchunks": dz,
+    }
+
+
 # --------------------------------------------------------------------- reference arm
 def run_reference(args, N):
     ws, rank, _ = dist_env()
@@ -314,6 +378,8 @@ def run_ours(args, N):
         "e2e": e2e,
         "nonfinite": nonfinite,
     }
+    if not args.no_ensemble and ws == 1:
+        line["ensemble"] = run_ensemble(torch)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if dist is not None:
@@ -334,6 +400,7 @@ def main():
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per CTA (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warm-up must be at least 3 steps", file=sys.stderr)

@@ -66,7 +66,8 @@ enum {
     AHS_OPT_PROFILE = 5,       /* 1: time every step-kernel launch with CUDA events            */
     AHS_OPT_N = 6,             /* lattice side (read only)                                     */
     AHS_OPT_TILE_Y = 7,        /* step-kernel tile height: 8 or 16 rows of 32 sites; 0 = auto   */
-    AHS_OPT_ZCHUNK = 8         /* z planes one CTA marches through, 1..N; 0 = auto            */
+    AHS_OPT_ZCHUNK = 8,        /* z planes one CTA marches through, 1..N; 0 = auto            */
+    AHS_OPT_GRAPH = 9          /* batches: 1 = replay each measurement period as a CUDA graph  */
 };
 
 typedef struct ahs ahs_t;
@@ -171,6 +172,59 @@ int ahs_kernel_time(ahs_t *h, int kind, double *ms_total, int64_t *launches, int
 
 /* ahs_device_bytes -- device memory held by the handle. */
 int ahs_device_bytes(ahs_t *h, size_t *bytes);
+
+/* ---- batched ensembles ---------------------------------------------------
+ * Many independent realisations (members) of possibly different sides N and
+ * eras, sharing dx, dt, lambda0, e0, sigma and s, advanced together: every
+ * leapfrog step is one persistent launch over the tiles of all members, and each
+ * measurement period (AHS_OPT_MEASURE_EVERY steps, 10 if measurements are off)
+ * is replayed as one captured CUDA graph.  A member runs the same kernel and
+ * coefficients as a single lattice, so its fields equal those of an ahs_t run of
+ * the same seed and launch shape bit for bit.  All members start at n = 0; member
+ * m stops at its last step n_end[m] (default: half light-crossing, eta_end =
+ * N dx / 2, Sec. 2) while the others continue.  Device memory: 80 bytes per site
+ * of every member plus small tables; the batch owns a non-blocking stream. */
+typedef struct ahs_batch ahs_batch_t;
+
+/* count members with sides N[m] in [4, 512], eras era[m], seeds seed[m] and last
+ * steps n_end[m] (NULL: half light-crossing).  NULL on error. */
+ahs_batch_t *ahs_batch_create(int count, const int *N, const int *era, const uint64_t *seed,
+                              const int64_t *n_end, double dx, double dt, double lambda0, double e0,
+                              double sigma, double s);
+/* random-phase initial condition of every member from its seed (as ahs_init) */
+int ahs_batch_init(ahs_batch_t *b);
+/* advance every member that has not reached its last step by up to max_steps
+ * steps; returns the number of steps advanced (0 when all are done) or a
+ * negative status (AHS_ENONFINITE after the steps if a measurement found one). */
+int ahs_batch_run(ahs_batch_t *b, int max_steps);
+/* measurement log of member m (as ahs_records) */
+int ahs_batch_records(ahs_batch_t *b, int m, ahs_obs_t *out, int max);
+/* fields of member m at its current time (as ahs_fields / ahs_set_fields) */
+int ahs_batch_fields(ahs_batch_t *b, int m, int which, void *host_dst, size_t bytes);
+int ahs_batch_set_fields(ahs_batch_t *b, int m, int which, const void *host_src, size_t bytes);
+/* current time level and last step of member m */
+int ahs_batch_step_info(ahs_batch_t *b, int m, int64_t *n, int64_t *n_end);
+/* options: MEASURE_EVERY (change only on a multiple of the old cadence), ALPHA,
+ * TAU0, WRAP_THETA, PROFILE, TILE_Y (8/16), ZCHUNK (all members; 0 = auto), GRAPH */
+int ahs_batch_set_option(ahs_batch_t *b, int key, double value);
+int ahs_batch_get_option(ahs_batch_t *b, int key, double *value);
+/* z-chunk member m currently uses */
+int ahs_batch_member_zchunk(ahs_batch_t *b, int m, int *dz);
+/* choose the tile height and each member size's z-chunk by timing the batched
+ * plain step itself (CUDA events on the batch stream; the state is not changed):
+ * per tile height, each size's z-chunk in turn with the others held fixed.
+ * Needs an initialised batch. */
+int ahs_batch_autotune(ahs_batch_t *b);
+/* with AHS_OPT_PROFILE: device time of ahs_batch_run calls (ms, CUDA events on the
+ * batch stream) and the steps they advanced */
+int ahs_batch_kernel_time(ahs_batch_t *b, double *ms_total, int64_t *steps, int reset);
+/* run on the caller's non-default stream instead of the batch's own */
+int ahs_batch_set_stream(ahs_batch_t *b, void *cuda_stream);
+void ahs_batch_destroy(ahs_batch_t *b);
+
+/* ahs_autotune -- choose AHS_OPT_TILE_Y and AHS_OPT_ZCHUNK of a single lattice by
+ * timing its plain step (CUDA events, the state is not changed); needs fields. */
+int ahs_autotune(ahs_t *h);
 
 /* ahs_measure_noalloc -- the measurement of ahs_measure on fields the caller
  * owns, without allocating any device memory.  The paper has no counterpart: this

@@ -94,6 +94,62 @@ class Lattice:
     def windings(self):
         return _abi.ahs_windings(self.h)
 
+    def autotune(self):
+        _abi.ahs_autotune(self.h)
 
-__all__ = ["Lattice", "AHSError", "ERAS", "AHS_FIELD_ALL", "AHS_FIELD_E", "AHS_FIELD_PHI",
+
+class Batch:
+    """An ensemble of independent lattices advanced together (one persistent launch
+    per step, each measurement period replayed as a CUDA graph)."""
+
+    def __init__(self, N, era, seed, n_end=None, dx: float = 0.5, dt: float = 0.1, lambda0: float = 2.0,
+                 e0: float = 1.0, sigma: float = 1.0, s: float = 0.0, measure_every: int = 10):
+        era = [ERAS.get(e, e) if isinstance(e, str) else e for e in era]
+        self.N = list(N)
+        self.b = _abi.ahs_batch_create(self.N, era, seed, n_end, dx, dt, lambda0, e0, sigma, s)
+        _abi.ahs_batch_set_option(self.b, _abi.AHS_OPT_MEASURE_EVERY, measure_every)
+
+    def close(self):
+        if getattr(self, "b", None):
+            _abi.ahs_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self):
+        _abi.ahs_batch_init(self.b)
+
+    def run(self, max_steps: int = 1 << 30) -> int:
+        return _abi.ahs_batch_run(self.b, max_steps)
+
+    def records(self, m: int):
+        return _abi.ahs_batch_records(self.b, m)
+
+    def state(self, m: int) -> np.ndarray:
+        return _abi.ahs_batch_fields(self.b, m, AHS_FIELD_ALL, self.N[m])
+
+    def set_state(self, m: int, F: np.ndarray):
+        _abi.ahs_batch_set_fields(self.b, m, AHS_FIELD_ALL, F)
+
+    def step_info(self, m: int):
+        return _abi.ahs_batch_step_info(self.b, m)
+
+    def set_option(self, key: int, value: float):
+        _abi.ahs_batch_set_option(self.b, key, value)
+
+    def autotune(self):
+        _abi.ahs_batch_autotune(self.b)
+
+
+__all__ = ["Lattice", "Batch", "AHSError", "ERAS", "AHS_FIELD_ALL", "AHS_FIELD_E", "AHS_FIELD_PHI",
            "AHS_FIELD_PI", "AHS_FIELD_THETA", "AHS_MATTER", "AHS_MINKOWSKI", "AHS_RADIATION"]

@@ -19,7 +19,7 @@ AHS_MINKOWSKI, AHS_RADIATION, AHS_MATTER = 0, 1, 2
 AHS_FIELD_PHI, AHS_FIELD_PI, AHS_FIELD_THETA, AHS_FIELD_E, AHS_FIELD_ALL = 0, 1, 2, 3, 4
 FIELD_PLANES = {AHS_FIELD_PHI: 2, AHS_FIELD_PI: 2, AHS_FIELD_THETA: 3, AHS_FIELD_E: 3, AHS_FIELD_ALL: 10}
 (AHS_OPT_MEASURE_EVERY, AHS_OPT_ALPHA, AHS_OPT_TAU0, AHS_OPT_STEP, AHS_OPT_WRAP_THETA,
- AHS_OPT_PROFILE, AHS_OPT_N, AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK) = range(9)
+ AHS_OPT_PROFILE, AHS_OPT_N, AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK, AHS_OPT_GRAPH) = range(10)
 AHS_KERNEL_STEP, AHS_KERNEL_STEP_MEASURE = 0, 1
 
 # every symbol include/ahs.h declares
@@ -27,8 +27,14 @@ EXPORTS = (
     "ahs_create", "ahs_init", "ahs_step", "ahs_measure", "ahs_records", "ahs_fields",
     "ahs_set_fields", "ahs_fields_box", "ahs_windings", "ahs_set_option", "ahs_get_option",
     "ahs_set_stream", "ahs_kernel_time", "ahs_device_bytes", "ahs_destroy", "ahs_last_error",
-    "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs", "ahs_measure_noalloc",
+    "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs", "ahs_measure_noalloc", "ahs_autotune",
+    "ahs_batch_create", "ahs_batch_init", "ahs_batch_run", "ahs_batch_records", "ahs_batch_fields",
+    "ahs_batch_set_fields", "ahs_batch_step_info", "ahs_batch_set_option", "ahs_batch_get_option",
+    "ahs_batch_member_zchunk", "ahs_batch_autotune", "ahs_batch_kernel_time", "ahs_batch_set_stream",
+    "ahs_batch_destroy",
 )
+_NON_INT = ("ahs_create", "ahs_destroy", "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs",
+            "ahs_batch_create", "ahs_batch_destroy")
 
 
 class ahs_obs_t(ctypes.Structure):
@@ -89,8 +95,27 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ahs_strerror.restype = ctypes.c_char_p
     L.ahs_sizeof_obs.restype = sz
     L.ahs_measure_noalloc.argtypes = [i, d, d, d, d, d, d, i, d, d, ctypes.c_int64, vp, vp, vp]
+    L.ahs_autotune.argtypes = [H]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    L.ahs_batch_create.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_uint64), i64p,
+                                   d, d, d, d, d, d]
+    L.ahs_batch_create.restype = H
+    L.ahs_batch_init.argtypes = [H]
+    L.ahs_batch_run.argtypes = [H, i]
+    L.ahs_batch_records.argtypes = [H, i, ctypes.POINTER(ahs_obs_t), i]
+    L.ahs_batch_fields.argtypes = [H, i, i, vp, sz]
+    L.ahs_batch_set_fields.argtypes = [H, i, i, vp, sz]
+    L.ahs_batch_step_info.argtypes = [H, i, i64p, i64p]
+    L.ahs_batch_set_option.argtypes = [H, i, d]
+    L.ahs_batch_get_option.argtypes = [H, i, ctypes.POINTER(d)]
+    L.ahs_batch_member_zchunk.argtypes = [H, i, ctypes.POINTER(i)]
+    L.ahs_batch_autotune.argtypes = [H]
+    L.ahs_batch_kernel_time.argtypes = [H, ctypes.POINTER(d), i64p, i]
+    L.ahs_batch_set_stream.argtypes = [H, vp]
+    L.ahs_batch_destroy.argtypes = [H]
+    L.ahs_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("ahs_create", "ahs_destroy", "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs"):
+        if name not in _NON_INT:
             getattr(L, name).restype = i
     if L.ahs_sizeof_obs() != ctypes.sizeof(ahs_obs_t):
         raise ImportError("ahs_obs_t layout mismatch between include/ahs.h and the binding")
@@ -204,3 +229,89 @@ def ahs_device_bytes(h) -> int:
 def ahs_destroy(h):
     if h:
         lib().ahs_destroy(h)
+
+
+def ahs_autotune(h):
+    return check(lib().ahs_autotune(h), "ahs_autotune")
+
+
+# ---- batched ensembles --------------------------------------------------------
+def ahs_batch_create(N, era, seed, n_end=None, dx=0.5, dt=0.1, lambda0=2.0, e0=1.0, sigma=1.0, s=0.0):
+    count = len(N)
+    Na = (ctypes.c_int * count)(*N)
+    Ea = (ctypes.c_int * count)(*era)
+    Sa = (ctypes.c_uint64 * count)(*seed)
+    Ta = (ctypes.c_int64 * count)(*n_end) if n_end is not None else None
+    h = lib().ahs_batch_create(count, Na, Ea, Sa, Ta, dx, dt, lambda0, e0, sigma, s)
+    if not h:
+        check(lib().ahs_last_error() or AHS_EINVAL, "ahs_batch_create")
+    return h
+
+
+def ahs_batch_init(b):
+    return check(lib().ahs_batch_init(b), "ahs_batch_init")
+
+
+def ahs_batch_run(b, max_steps):
+    return check(lib().ahs_batch_run(b, max_steps), "ahs_batch_run")
+
+
+def ahs_batch_records(b, m):
+    pending = check(lib().ahs_batch_records(b, m, None, 0), "ahs_batch_records")
+    if pending == 0:
+        return []
+    buf = (ahs_obs_t * pending)()
+    got = check(lib().ahs_batch_records(b, m, buf, pending), "ahs_batch_records")
+    return [buf[k].as_dict() for k in range(got)]
+
+
+def ahs_batch_step_info(b, m):
+    n, e = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().ahs_batch_step_info(b, m, ctypes.byref(n), ctypes.byref(e)), "ahs_batch_step_info")
+    return n.value, e.value
+
+
+def ahs_batch_fields(b, m, which, N) -> np.ndarray:
+    out = np.empty((FIELD_PLANES[which], N, N, N), dtype=np.float32)
+    check(lib().ahs_batch_fields(b, m, which, out.ctypes.data, out.nbytes), "ahs_batch_fields")
+    return out
+
+
+def ahs_batch_set_fields(b, m, which, src: np.ndarray):
+    src = np.ascontiguousarray(src, dtype=np.float32)
+    return check(lib().ahs_batch_set_fields(b, m, which, src.ctypes.data, src.nbytes), "ahs_batch_set_fields")
+
+
+def ahs_batch_set_option(b, key, value):
+    return check(lib().ahs_batch_set_option(b, key, float(value)), "ahs_batch_set_option")
+
+
+def ahs_batch_get_option(b, key) -> float:
+    v = ctypes.c_double()
+    check(lib().ahs_batch_get_option(b, key, ctypes.byref(v)), "ahs_batch_get_option")
+    return v.value
+
+
+def ahs_batch_member_zchunk(b, m) -> int:
+    v = ctypes.c_int()
+    check(lib().ahs_batch_member_zchunk(b, m, ctypes.byref(v)), "ahs_batch_member_zchunk")
+    return v.value
+
+
+def ahs_batch_autotune(b):
+    return check(lib().ahs_batch_autotune(b), "ahs_batch_autotune")
+
+
+def ahs_batch_kernel_time(b, reset=False):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    check(lib().ahs_batch_kernel_time(b, ctypes.byref(ms), ctypes.byref(n), int(reset)), "ahs_batch_kernel_time")
+    return ms.value, n.value
+
+
+def ahs_batch_set_stream(b, stream_ptr: int):
+    return check(lib().ahs_batch_set_stream(b, ctypes.c_void_p(stream_ptr)), "ahs_batch_set_stream")
+
+
+def ahs_batch_destroy(b):
+    if b:
+        lib().ahs_batch_destroy(b)

@@ -3,7 +3,7 @@
 // Owns the device state of one lattice, turns the step index into the FP64
 // scalars of Eqs. 7-8 and 11-12 (rounded once to float32 for the stencil), and
 // sequences the step, reduction and copy launches on the handle's stream.
-#include "ahs_internal.cuh"
+#include "ahs_host.h"
 
 #include <cmath>
 #include <cstdarg>
@@ -42,7 +42,6 @@ int ok()
         if (e_ != cudaSuccess) return fail(AHS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-constexpr double kPi = 3.141592653589793238;
 constexpr int kFields = 10;   // Re phi, Im phi, Re Pi, Im Pi, theta_xyz, E_xyz
 
 }  // namespace
@@ -53,14 +52,9 @@ int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
 int report_ok() { return ok(); }
 }  // namespace eng
 
-struct ahs {
-    int N = 0;
+struct ahs : eng::LatticeParams {
     size_t V = 0;
-    double dx = 0.5, dt = 0.1, lambda0 = 2.0, e0 = 1.0, sigma = 1.0, s = 0.0;
-    int era = 1;
-    double alpha = 2.0, tau0 = 1.0;
     int measure_every = 10;
-    int wrap = 0;
     int profile = 0;
     int64_t n = 0;        // integer time level of phi/theta in buffer `cur`
     int cur = 0;
@@ -86,48 +80,6 @@ struct ahs {
 
 namespace {
 
-// FP64 scalars of step n (Eqs. 7, 8, 11, 12): eta, a, delta, omega, c = a^{2s}
-struct Scalars {
-    double eta, a, delta, omega, c;
-};
-
-Scalars scalars(const ahs_t *h, int64_t n)
-{
-    Scalars r;
-    r.eta = h->tau0 + (double)n * h->dt;
-    r.a = std::pow(r.eta / h->tau0, (double)h->era);
-    r.delta = 0.5 * h->alpha * (double)h->era * h->dt / r.eta;
-    r.omega = r.delta * (1.0 - h->s);
-    r.c = std::pow(r.a, 2.0 * h->s);
-    return r;
-}
-
-StepCoef coefficients(const ahs_t *h, int64_t n)
-{
-    const Scalars S = scalars(h, n);
-    const double dx = h->dx, dt = h->dt;
-    StepCoef k;
-    k.cpi = (float)((1.0 - S.delta) / (1.0 + S.delta));
-    k.kpi_lap = (float)(dt / ((1.0 + S.delta) * dx * dx));
-    k.kpi_pot = (float)(dt * 0.5 * h->lambda0 * S.c / (1.0 + S.delta));
-    k.sigma2 = (float)(h->sigma * h->sigma);
-    k.ce = (float)((1.0 - S.omega) / (1.0 + S.omega));
-    k.ke_curl = (float)(dt / ((1.0 + S.omega) * dx * dx * dx));
-    k.ke_cur = (float)(dt * 2.0 * h->e0 * h->e0 * S.c / ((1.0 + S.omega) * dx));
-    k.dphi = (float)dt;
-    k.dtheta = (float)(dt * dx);
-    k.wrap = h->wrap;
-    k.m_grad = (float)(1.0 / (dx * dx));
-    k.m_pot = (float)(0.25 * h->lambda0 * S.c);
-    k.m_el = (float)(1.0 / (2.0 * h->e0 * h->e0 * S.c));
-    k.m_mag = (float)(1.0 / (h->e0 * h->e0 * S.c * dx * dx * dx * dx));
-    const Scalars P = scalars(h, n - 1);   // the kick that produced the stored momenta
-    const double kappa = P.c * (1.0 + P.delta) / (1.0 + P.omega);
-    k.m_gauss = (float)(2.0 * h->e0 * h->e0 * kappa);
-    k.inv_dx = (float)(1.0 / dx);
-    return k;
-}
-
 StepPtrs pointers(const ahs_t *h)
 {
     const int a = h->cur, b = 1 - h->cur;
@@ -141,20 +93,6 @@ StepPtrs pointers(const ahs_t *h)
     p.tx1 = h->plane(b, 4); p.ty1 = h->plane(b, 5); p.tz1 = h->plane(b, 6);
     p.ex1 = h->plane(b, 7); p.ey1 = h->plane(b, 8); p.ez1 = h->plane(b, 9);
     return p;
-}
-
-ObsScalars obs_scalars(const ahs_t *h, int64_t n)
-{
-    const Scalars S = scalars(h, n);
-    ObsScalars o;
-    o.step = n;
-    o.tau = S.eta;
-    o.a = S.a;
-    o.dx = h->dx;
-    o.sites = (double)h->V;
-    o.volume = std::pow((double)h->N * h->dx, 3.0);
-    o.mu = 2.0 * kPi * h->sigma * h->sigma;
-    return o;
 }
 
 // field selector -> (first plane, number of planes)
@@ -567,6 +505,43 @@ int ahs_windings(ahs_t *h, int8_t *dst, size_t bytes, int64_t *n_wind)
         for (size_t i = 0; i < bytes; ++i) t += dst[i] < 0 ? -dst[i] : dst[i];
         *n_wind = t;
     }
+    return ok();
+}
+
+int ahs_autotune(ahs_t *h)
+{
+    if (!h) return fail(AHS_EINVAL, "null handle");
+    if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
+    if (int r = set_device(h)) return r;
+    const StepCoef k = coefficients(h, h->n);
+    const StepPtrs p = pointers(h);
+    cudaEvent_t e0 = event_at(h, 0), e1 = event_at(h, 1);
+    if (!e0 || !e1) return fail(AHS_ECUDA, "cudaEventCreate failed");
+    const int bys[2] = {8, 16}, dzs[6] = {4, 8, 16, 32, 64, 128};
+    double best = 1e300;
+    int best_by = 8, best_dz = 0;
+    for (int by : bys)
+        for (int dz : dzs) {
+            if (dz > h->N) continue;
+            const StepShape sh = step_shape(h->N, by, dz);
+            CU(launch_step(p, k, h->N, sh, false, true, nullptr, h->stream));   // warm-up
+            float tot = 0.f, ms = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                CU(cudaEventRecord(e0, h->stream));
+                CU(launch_step(p, k, h->N, sh, false, true, nullptr, h->stream));
+                CU(cudaEventRecord(e1, h->stream));
+                CU(cudaEventSynchronize(e1));
+                CU(cudaEventElapsedTime(&ms, e0, e1));
+                tot += ms;
+            }
+            if (tot < best) {
+                best = tot;
+                best_by = by;
+                best_dz = dz;
+            }
+        }
+    h->tile_y = best_by;
+    h->zchunk = best_dz;
     return ok();
 }
 

@@ -77,6 +77,44 @@ cudaError_t launch_windings(const float *pr, const float *pim, const float *tx, 
 cudaError_t launch_gather_box(const float *const *planes, int nplanes, int N, int x0, int y0, int z0,
                               int nx, int ny, int nz, float *dst, cudaStream_t st);
 
+// ---- batched ensembles: many lattices advanced by one persistent launch -------
+// One tile of work (the 32 x BY column at (x0, y0), planes [z0, zend)) of member
+// `member`; its measurement partials go to the row with the tile's index.
+struct BatchTile {
+    int member, x0, y0, z0, zend, pad;
+};
+// A member lattice: its two field buffers (base: buffer 0 Re phi; the twenty
+// planes of N^3 floats follow each other, buffer 1 starting at plane 10), side,
+// last step, and its rows of measurement partials.  Members have 20 N^3 < 2^32.
+struct BatchMember {
+    const float *base;
+    int N, row0, nrows, pad;
+    int64_t n_end;
+};
+// Everything one batched step launch reads.  The step index is *counter + dn
+// (dn is fixed when a launch is recorded into a graph); coefficients come from a
+// table computed on the host in FP64, coef[member * coef_stride + n].
+struct BatchLaunch {
+    const BatchTile *tiles;
+    int ntiles;
+    const int *live;          // live[n]: tiles of members still running at step n (a prefix of the list)
+    int *tickets;             // tickets[n]: next unclaimed tile of step n (zero before the step)
+    const BatchMember *members;
+    int nmembers;
+    const StepCoef *coef;
+    int coef_stride;
+    const int64_t *counter;
+    double *partials;
+};
+cudaError_t launch_batch_step(const BatchLaunch &L, int by, int dn, bool measure, int grid, cudaStream_t st);
+int batch_grid(int by, bool measure);   // resident CTAs of the persistent launch
+// per-member measurement record of step *counter + dn when that step is a
+// measurement step of the member: records[m * rcap + n / every]
+cudaError_t launch_batch_reduce(const double *partials, const BatchMember *members, int nmembers,
+                                const ObsScalars *obs, int obs_stride, const int64_t *counter, int dn, int every,
+                                ahs_obs_t *records, int rcap, cudaStream_t st);
+cudaError_t launch_advance(int64_t *counter, int64_t delta, cudaStream_t st);
+
 // error state of the C ABI (ahs_last_error / ahs_last_error_message)
 int report_error(int code, const char *msg);
 int report_ok();

@@ -111,8 +111,7 @@ __global__ void gather_box_kernel(PlaneList L, int nplanes, int N, int x0, int y
 // ---------------------------------------------------------------- final reduction
 constexpr int RT = 256;
 
-__global__ void __launch_bounds__(RT) reduce_kernel(const double *__restrict__ part, int nb, ObsScalars sc,
-                                                    ahs_obs_t *rec)
+__device__ void reduce_rows(const double *__restrict__ part, int nb, const ObsScalars &sc, ahs_obs_t *rec)
 {
     __shared__ double sh[RT][NQ + 1];
     const int t = threadIdx.x;
@@ -167,6 +166,30 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const double *__restrict__ p
     }
 }
 
+__global__ void __launch_bounds__(RT) reduce_kernel(const double *__restrict__ part, int nb, ObsScalars sc,
+                                                    ahs_obs_t *rec)
+{
+    reduce_rows(part, nb, sc, rec);
+}
+
+// one CTA per member: the record of step *counter + dn for members still running
+__global__ void __launch_bounds__(RT) batch_reduce_kernel(const double *__restrict__ part, const BatchMember *members,
+                                                          const ObsScalars *obs, int obs_stride,
+                                                          const int64_t *counter, int dn, int every,
+                                                          ahs_obs_t *records, int rcap)
+{
+    const int m = blockIdx.x;
+    const int64_t n = *counter + dn;
+    const BatchMember &mb = members[m];
+    if (n >= mb.n_end || every <= 0 || n % every != 0) return;
+    const int slot = (int)(n / every);
+    if (slot >= rcap || slot >= obs_stride) return;
+    reduce_rows(part + (size_t)mb.row0 * NQ, mb.nrows, obs[(size_t)m * obs_stride + slot],
+                records + (size_t)m * rcap + slot);
+}
+
+__global__ void advance_kernel(int64_t *counter, int64_t delta) { *counter += delta; }
+
 }  // namespace
 
 cudaError_t launch_init(float *pr, float *pim, int N, uint64_t seed, double sigma, cudaStream_t st)
@@ -183,6 +206,20 @@ cudaError_t launch_reduce(const double *partials, int nblocks, const ObsScalars 
                           cudaStream_t st)
 {
     reduce_kernel<<<1, RT, 0, st>>>(partials, nblocks, sc, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_reduce(const double *partials, const BatchMember *members, int nmembers,
+                                const ObsScalars *obs, int obs_stride, const int64_t *counter, int dn, int every,
+                                ahs_obs_t *records, int rcap, cudaStream_t st)
+{
+    batch_reduce_kernel<<<nmembers, RT, 0, st>>>(partials, members, obs, obs_stride, counter, dn, every, records, rcap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(int64_t *counter, int64_t delta, cudaStream_t st)
+{
+    advance_kernel<<<1, 1, 0, st>>>(counter, delta);
     return cudaGetLastError();
 }
 

@@ -69,25 +69,61 @@ __device__ __forceinline__ int wrapN(int v, int N)
     return v < 0 ? v + N : v;
 }
 
-__device__ __forceinline__ Raw load_raw(const StepPtrs &P, uint32_t o)
+// Field access of one step, in the plane order of a buffer: 0 Re phi, 1 Im phi,
+// 2 Re Pi, 3 Im Pi, 4-6 theta_xyz, 7-9 E_xyz; `in` reads the time-n buffer,
+// `out` writes the n+1 buffer.  ParamFields takes the twenty plane pointers of a
+// single lattice (kernel parameters, constant bank); ArenaFields addresses the
+// two buffers of one member of a batch from one base pointer with 32-bit plane
+// offsets (requires 20 N^3 < 2^32).
+enum { FPR = 0, FPI, FQR, FQI, FTX, FTY, FTZ, FEX, FEY, FEZ };
+
+struct ParamFields {
+    const StepPtrs &P;
+    __device__ __forceinline__ float in(int f, uint32_t o) const
+    {
+        const float *p = f == FPR ? P.pr : f == FPI ? P.pim : f == FQR ? P.qr : f == FQI ? P.qi : f == FTX ? P.tx
+                       : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : P.ez;
+        return __ldg(p + o);
+    }
+    __device__ __forceinline__ void out(int f, uint32_t o, float v) const
+    {
+        float *p = f == FPR ? P.pr1 : f == FPI ? P.pim1 : f == FQR ? P.qr1 : f == FQI ? P.qi1 : f == FTX ? P.tx1
+                 : f == FTY ? P.ty1 : f == FTZ ? P.tz1 : f == FEX ? P.ex1 : f == FEY ? P.ey1 : P.ez1;
+        p[o] = v;
+    }
+};
+
+struct ArenaFields {
+    const float *base;       // the member's first plane (buffer 0, Re phi)
+    uint32_t in0, out0, V;   // plane offsets of the read and write buffers, plane size
+    __device__ __forceinline__ float in(int f, uint32_t o) const { return __ldg(base + (in0 + (uint32_t)f * V + o)); }
+    __device__ __forceinline__ void out(int f, uint32_t o, float v) const
+    {
+        const_cast<float *>(base)[out0 + (uint32_t)f * V + o] = v;
+    }
+};
+
+template <class FA>
+__device__ __forceinline__ Raw load_raw(const FA &P, uint32_t o)
 {
     Raw a;
-    a.tx = __ldg(P.tx + o);
-    a.ty = __ldg(P.ty + o);
-    a.tz = __ldg(P.tz + o);
-    a.pr = __ldg(P.pr + o);
-    a.pi = __ldg(P.pim + o);
+    a.tx = P.in(FTX, o);
+    a.ty = P.in(FTY, o);
+    a.tz = P.in(FTZ, o);
+    a.pr = P.in(FPR, o);
+    a.pi = P.in(FPI, o);
     return a;
 }
 
-__device__ __forceinline__ PE load_pe(const StepPtrs &P, uint32_t o)
+template <class FA>
+__device__ __forceinline__ PE load_pe(const FA &P, uint32_t o)
 {
     PE a;
-    a.qr = __ldg(P.qr + o);
-    a.qi = __ldg(P.qi + o);
-    a.ex = __ldg(P.ex + o);
-    a.ey = __ldg(P.ey + o);
-    a.ez = __ldg(P.ez + o);
+    a.qr = P.in(FQR, o);
+    a.qi = P.in(FQI, o);
+    a.ex = P.in(FEX, o);
+    a.ey = P.in(FEY, o);
+    a.ez = P.in(FEZ, o);
     return a;
 }
 
@@ -109,16 +145,15 @@ __device__ __forceinline__ float2 plaquette(float2 vi, float2 vj, float2 vjp, fl
 
 __device__ __forceinline__ int next_plane(int z, int N) { return z + 1 == N ? 0 : z + 1; }
 
-template <int BY, bool MEASURE, bool STORE>
-__global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, int N, int Dz, double *partials)
+// One tile: the 32 x BY column at (x0, y0), planes [z0, zend).  All threads of the
+// CTA call it together (it contains CTA barriers); with MEASURE the CTA's FP64
+// partial sums go to `partial_row`.
+template <int BY, bool MEASURE, bool STORE, class FA>
+__device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &P, const StepCoef &k, int N,
+                                          int x0, int y0, int z0, int zend, double *partial_row)
 {
     using T = Tile<BY>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
-
     const int tx = threadIdx.x, ty = threadIdx.y, t = tx + 32 * ty;
-    const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
-    const int zend = min(z0 + Dz, N);
     const uint32_t NN = (uint32_t)N * (uint32_t)N;
 
     // core item: this thread's own site; ring items of phases A and B
@@ -174,7 +209,7 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
     if (hasA) rh = load_raw(P, (uint32_t)z1 * NN + haoff);
     PE pe_next{}, pe_cur{};
     float ezPrev = 0.f;
-    if (MEASURE) ezPrev = __ldg(P.ez + (uint32_t)zc * NN + coff);
+    if (MEASURE) ezPrev = P.in(FEZ, (uint32_t)zc * NN + coff);
 
     // carried from plane zz-1 (own column)
     float2 phPrev = make_float2(0.f, 0.f), vzPrev = make_float2(1.f, 0.f);
@@ -238,15 +273,15 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
                 const float2 hp = pc.ph[rh0];
                 if (ringRow) {   // row BY: Y_x
                     const float2 q = pc.ph[T::r(hyx + 1, hyy)], v = pc.vx[rh0];
-                    S.yx[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return __ldg(P.tx + ho); });
+                    S.yx[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTX, ho); });
                 } else {         // column BX: Y_y
                     const float2 q = pc.ph[T::r(hyx, hyy + 1)], v = pc.vy[rh0];
-                    S.yy[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return __ldg(P.ty + ho); });
+                    S.yy[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTY, ho); });
                 }
                 const float2 q = pn.ph[rh0], v = pc.vz[rh0];
-                S.yz[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return __ldg(P.tz + ho); });
-                if (ringRow) S.ey[T::q(hbx, hby)] = __ldg(P.ey + oc + hboff);
-                else S.ex[T::q(hbx, hby)] = __ldg(P.ex + oc + hboff);
+                S.yz[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTZ, ho); });
+                if (ringRow) S.ey[T::q(hbx, hby)] = P.in(FEY, oc + hboff);
+                else S.ex[T::q(hbx, hby)] = P.in(FEX, oc + hboff);
             }
         }
         __syncthreads();
@@ -321,11 +356,11 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
                 const float tnx = nthx, tny = nthy;
                 const float t0x = thx, t0y = thy, t0z = thz;
                 const float wxy = wrap_from_q(Qxy.x, Qxy.y, [&](float &a, float &bb, float &c, float &d) {
-                    a = t0x; bb = __ldg(P.ty + oc + cxpoff); c = __ldg(P.tx + oc + cypoff); d = t0y; });
+                    a = t0x; bb = P.in(FTY, oc + cxpoff); c = P.in(FTX, oc + cypoff); d = t0y; });
                 const float wxz = wrap_from_q(Qxz.x, Qxz.y, [&](float &a, float &bb, float &c, float &d) {
-                    a = t0x; bb = __ldg(P.tz + oc + cxpoff); c = tnx; d = t0z; });
+                    a = t0x; bb = P.in(FTZ, oc + cxpoff); c = tnx; d = t0z; });
                 const float wyz = wrap_from_q(Qyz.x, Qyz.y, [&](float &a, float &bb, float &c, float &d) {
-                    a = t0y; bb = __ldg(P.tz + oc + cypoff); c = tny; d = t0z; });
+                    a = t0y; bb = P.in(FTZ, oc + cypoff); c = tny; d = t0z; });
                 const int nxy = winding(Yx, S.yy[T::w(tx + 1, ty)], S.yx[T::w(tx, ty + 1)], Yy, wxy);
                 const int nxz = winding(Yx, S.yz[T::w(tx + 1, ty)], YxNext, Yz, wxz);
                 const int nyz = winding(Yy, S.yz[T::w(tx, ty + 1)], YyNext, Yz, wyz);
@@ -334,22 +369,22 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
 
             if (STORE) {
                 const uint32_t o = oc + coff;
-                P.qr1[o] = qnr;
-                P.qi1[o] = qni;
-                P.ex1[o] = enx;
-                P.ey1[o] = eny;
-                P.ez1[o] = enz;
-                P.pr1[o] = p0.x + k.dphi * qnr;
-                P.pim1[o] = p0.y + k.dphi * qni;
+                P.out(FQR, o, qnr);
+                P.out(FQI, o, qni);
+                P.out(FEX, o, enx);
+                P.out(FEY, o, eny);
+                P.out(FEZ, o, enz);
+                P.out(FPR, o, p0.x + k.dphi * qnr);
+                P.out(FPI, o, p0.y + k.dphi * qni);
                 float t1x = thx + k.dtheta * enx, t1y = thy + k.dtheta * eny, t1z = thz + k.dtheta * enz;
                 if (k.wrap) {
                     t1x += kTwoPiF * floorf((kPiF - t1x) * kInvTwoPiF);
                     t1y += kTwoPiF * floorf((kPiF - t1y) * kInvTwoPiF);
                     t1z += kTwoPiF * floorf((kPiF - t1z) * kInvTwoPiF);
                 }
-                P.tx1[o] = t1x;
-                P.ty1[o] = t1y;
-                P.tz1[o] = t1z;
+                P.out(FTX, o, t1x);
+                P.out(FTY, o, t1y);
+                P.out(FTZ, o, t1z);
             }
         }
         // carry plane zz's own-column values to plane zz+1
@@ -366,10 +401,81 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
         __syncthreads();
     }
 
-    if (MEASURE) {
-        const size_t bi = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-        block_reduce_store<32 * BY>(acc, partials + bi * NQ);
+    if (MEASURE) block_reduce_store<32 * BY>(acc, partial_row);
+}
+
+template <int BY, bool MEASURE, bool STORE>
+__global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, int N, int Dz, double *partials)
+{
+    using T = Tile<BY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
+    const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
+    const size_t bi = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+    tile_step<BY, MEASURE, STORE>(S, ParamFields{P}, k, N, x0, y0, z0, min(z0 + Dz, N),
+                                  MEASURE ? partials + bi * NQ : nullptr);
+}
+
+// Persistent batched step: every CTA claims tiles of the work list one at a time
+// from the step's ticket counter (so tiles of unequal cost balance dynamically)
+// and runs them; the list is ordered by the members' last step, so at step n the
+// tiles of members still running form the prefix live[n].  The member's field
+// base and coefficients are staged per tile.
+template <int BY, bool MEASURE>
+__global__ void __launch_bounds__(32 * BY, (MEASURE ? 16 : 24) / BY) batch_step(BatchLaunch L, int dn)
+{
+    using T = Tile<BY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
+    __shared__ StepCoef sk;
+    __shared__ int s_w;
+    const int64_t n = *L.counter + dn;
+    const int par = (int)(n & 1);
+    const int live = L.live[n];
+    const int t = threadIdx.x + 32 * threadIdx.y;
+    for (;;) {
+        __syncthreads();   // everyone is done with s_w and sk of the previous tile
+        if (t == 0) s_w = atomicAdd(L.tickets + n, 1);
+        __syncthreads();
+        const int w = s_w;
+        if (w >= live) break;
+        const BatchTile tl = L.tiles[w];
+        const BatchMember &m = L.members[tl.member];
+        if (t < (int)(sizeof(StepCoef) / sizeof(float)))
+            reinterpret_cast<float *>(&sk)[t] = reinterpret_cast<const float *>(L.coef + (size_t)tl.member * L.coef_stride + n)[t];
+        const uint32_t V = (uint32_t)m.N * (uint32_t)m.N * (uint32_t)m.N;
+        const ArenaFields fa{m.base, par ? 10u * V : 0u, par ? 0u : 10u * V, V};
+        __syncthreads();
+        tile_step<BY, MEASURE, true>(S, fa, sk, m.N, tl.x0, tl.y0, tl.z0, tl.zend,
+                                     MEASURE ? L.partials + (size_t)w * NQ : nullptr);
     }
+}
+
+template <int BY, bool MEASURE>
+int batch_occupancy()
+{
+    using T = Tile<BY>;
+    const size_t bytes = MEASURE ? T::kMeasureBytes : T::kStepBytes;
+    if (cudaFuncSetAttribute(batch_step<BY, MEASURE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return 0;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step<BY, MEASURE>, 32 * BY, bytes) != cudaSuccess)
+        return 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return per_sm * sms;
+}
+
+template <int BY, bool MEASURE>
+cudaError_t launch_batch_variant(const BatchLaunch &L, int dn, int grid, cudaStream_t st)
+{
+    // the dynamic shared-memory limit was raised by batch_occupancy() when the
+    // launch was sized, before any launch or graph capture
+    using T = Tile<BY>;
+    const size_t bytes = MEASURE ? T::kMeasureBytes : T::kStepBytes;
+    batch_step<BY, MEASURE><<<grid, dim3(32, BY), bytes, st>>>(L, dn);
+    return cudaGetLastError();
 }
 
 template <int BY, bool M, bool S>
@@ -417,6 +523,19 @@ StepShape step_shape(int N, int tile_y, int zchunk)
     }
     s.blocks = ((N + 31) / 32) * ((N + s.by - 1) / s.by) * ((N + s.dz - 1) / s.dz);
     return s;
+}
+
+int batch_grid(int by, bool measure)
+{
+    if (by == 16) return measure ? batch_occupancy<16, true>() : batch_occupancy<16, false>();
+    return measure ? batch_occupancy<8, true>() : batch_occupancy<8, false>();
+}
+
+cudaError_t launch_batch_step(const BatchLaunch &L, int by, int dn, bool measure, int grid, cudaStream_t st)
+{
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    if (by == 16) return measure ? launch_batch_variant<16, true>(L, dn, grid, st) : launch_batch_variant<16, false>(L, dn, grid, st);
+    return measure ? launch_batch_variant<8, true>(L, dn, grid, st) : launch_batch_variant<8, false>(L, dn, grid, st);
 }
 
 cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, bool measure, bool store,

@@ -1,0 +1,121 @@
+"""Batched ensembles: members of uneven sizes and eras advanced by one persistent
+launch per step (graph-replayed measurement periods) equal single-lattice runs of
+the same seeds bit for bit, stop at their own last step, and match the oracle."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = dict(dx=0.5, dt=0.1, lambda0=2.0, e0=1.0, sigma=1.0)
+MEMBERS = [  # (N, era, seed, n_end)
+    (16, 1, 11, 25), (24, 2, 12, 17), (20, 0, 13, 30), (36, 1, 14, 22), (8, 2, 15, 9),
+]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2005_14454_gb300 as p
+    from paper_2005_14454_gb300 import _abi
+    _abi.lib()
+    return p
+
+
+def single(pkg, N, era, seed, steps, measure_every=5):
+    with pkg.Lattice(N, era=era, measure_every=measure_every, **PARAMS) as lat:
+        lat.init(seed)
+        lat.step(steps)
+        return lat.state(), lat.records()
+
+
+def make_batch(pkg, members=MEMBERS, measure_every=5):
+    N, era, seed, end = zip(*members)
+    return pkg.Batch(N, era, seed, list(end), measure_every=measure_every, **PARAMS)
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_batch_equals_single_runs(pkg, graph):
+    from paper_2005_14454_gb300._abi import AHS_OPT_GRAPH
+    with make_batch(pkg) as b:
+        b.set_option(AHS_OPT_GRAPH, graph)
+        b.init()
+        done = b.run()
+        assert done == max(m[3] for m in MEMBERS)
+        assert b.run() == 0
+        for i, (N, era, seed, end) in enumerate(MEMBERS):
+            n, n_end = b.step_info(i)
+            assert n == n_end == end
+            F, rec = single(pkg, N, era, seed, end)
+            assert np.array_equal(b.state(i), F), i
+            got = b.records(i)
+            assert [r["step"] for r in got] == [r["step"] for r in rec] == list(range(0, end, 5))
+            assert got == rec
+
+
+def test_batch_runs_in_pieces(pkg):
+    # uneven run lengths: graph periods and single steps interleave
+    with make_batch(pkg) as b1, make_batch(pkg) as b2:
+        b1.init()
+        b2.init()
+        b1.run()
+        for chunk in (3, 7, 1, 12, 100):
+            b2.run(chunk)
+        for i in range(len(MEMBERS)):
+            assert np.array_equal(b1.state(i), b2.state(i))
+            assert b1.records(i) == b2.records(i)
+
+
+def test_batch_member_matches_oracle(pkg, orc):
+    with make_batch(pkg, members=[(24, 1, 3, 10), (32, 2, 4, 10)]) as b:
+        b.init()
+        F0 = [b.state(i).astype(np.float64) for i in range(2)]
+        b.run()
+        for i, (N, era) in enumerate([(24, 1), (32, 2)]):
+            ref = F0[i].copy()
+            orc.run(orc.Params(N=N, era=era, **PARAMS), 0, 10, ref)
+            got = b.state(i).astype(np.float64)
+            for sl in (slice(0, 2), slice(2, 4), slice(7, 10)):
+                err = np.linalg.norm(got[sl] - ref[sl]) / np.linalg.norm(ref[sl])
+                assert err < 1e-5
+
+
+def test_batch_autotune_keeps_results(pkg):
+    from paper_2005_14454_gb300._abi import AHS_OPT_TILE_Y, ahs_batch_member_zchunk
+    with make_batch(pkg) as a, make_batch(pkg) as b:
+        a.init()
+        b.init()
+        b.autotune()
+        assert b.b and int(__import__("paper_2005_14454_gb300")._abi.ahs_batch_get_option(b.b, AHS_OPT_TILE_Y)) in (8, 16)
+        assert all(ahs_batch_member_zchunk(b.b, i) >= 1 for i in range(len(MEMBERS)))
+        a.run()
+        b.run()
+        for i in range(len(MEMBERS)):
+            assert np.array_equal(a.state(i), b.state(i))
+
+
+def test_batch_set_fields_and_nonfinite(pkg):
+    from paper_2005_14454_gb300 import AHSError
+    from paper_2005_14454_gb300._abi import AHS_ENONFINITE
+    with make_batch(pkg, members=[(16, 1, 1, 20), (12, 1, 2, 20)]) as b:
+        b.init()
+        F = b.state(1)
+        F[8, 2, 3, 4] = np.inf
+        b.set_state(1, F)
+        with pytest.raises(AHSError) as ei:
+            b.run(6)
+        assert ei.value.status == AHS_ENONFINITE
+        assert b.step_info(0)[0] == 6
+
+
+def test_batch_bad_arguments(pkg):
+    from paper_2005_14454_gb300 import AHSError
+    with pytest.raises(AHSError):
+        pkg.Batch([16, 3], [1, 1], [1, 2])
+    with pytest.raises(AHSError):
+        pkg.Batch([16], [5], [1])
+    with make_batch(pkg) as b:
+        with pytest.raises(AHSError):
+            b.run(1)          # not initialised
+        b.init()
+        from paper_2005_14454_gb300 import _abi
+        with pytest.raises(AHSError):
+            _abi.ahs_batch_fields(b.b, 99, _abi.AHS_FIELD_ALL, 16)
