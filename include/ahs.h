@@ -54,7 +54,17 @@ enum { AHS_MINKOWSKI = 0, AHS_RADIATION = 1, AHS_MATTER = 2 };
  * E 3 (x, y, z), ALL 10 in the order phi, Pi, theta, E.  phi and theta live at
  * the integer time n, Pi and E at n - 1/2. */
 enum { AHS_FIELD_PHI = 0, AHS_FIELD_PI = 1, AHS_FIELD_THETA = 2, AHS_FIELD_E = 3,
-       AHS_FIELD_ALL = 4 };
+       AHS_FIELD_ALL = 4,
+       AHS_FIELD_LOW = 5   /* compensated precision only: 5 planes, low words of Re Pi, Im Pi, E_xyz */ };
+
+/* ---- precision modes (AHS_OPT_PRECISION; changing it discards the fields) ----
+ * FP32: float32 storage and arithmetic, FP64 reductions (80 bytes/site).
+ * FP32_COMPENSATED: as FP32, with Pi and E held as float32 high + low words and
+ *   updated by compensated (error-free product and sum) arithmetic (120 bytes/site).
+ * FP64: double storage and arithmetic for every step (160 bytes/site); field copies
+ *   then move 8-byte values; box copies, the winding field and autotuning are not
+ *   available. */
+enum { AHS_PREC_FP32 = 0, AHS_PREC_FP32_COMPENSATED = 1, AHS_PREC_FP64 = 2 };
 
 /* ---- options for ahs_set_option / ahs_get_option ------------------------ */
 enum {
@@ -67,7 +77,8 @@ enum {
     AHS_OPT_N = 6,             /* lattice side (read only)                                     */
     AHS_OPT_TILE_Y = 7,        /* step-kernel tile height: 8 or 16 rows of 32 sites; 0 = auto   */
     AHS_OPT_ZCHUNK = 8,        /* z planes one CTA marches through, 1..N; 0 = auto            */
-    AHS_OPT_GRAPH = 9          /* batches: 1 = replay each measurement period as a CUDA graph  */
+    AHS_OPT_GRAPH = 9,         /* batches: 1 = replay each measurement period as a CUDA graph  */
+    AHS_OPT_PRECISION = 10     /* AHS_PREC_*; default FP32                                     */
 };
 
 typedef struct ahs ahs_t;
@@ -135,8 +146,9 @@ int ahs_measure(ahs_t *h, ahs_obs_t *out);
 int ahs_records(ahs_t *h, ahs_obs_t *out, int max);
 
 /* ahs_fields / ahs_set_fields -- copy one field (see the selectors) between the
- * device and a host buffer of exactly planes * N^3 * 4 bytes, planes in the
- * selector's order.  set_fields leaves the time level n unchanged. */
+ * device and a host buffer of exactly planes * N^3 * 4 bytes (8 in FP64 precision),
+ * planes in the selector's order.  set_fields leaves the time level n unchanged;
+ * in compensated precision, setting Pi or E clears their low words. */
 int ahs_fields(ahs_t *h, int which, void *host_dst, size_t bytes);
 int ahs_set_fields(ahs_t *h, int which, const void *host_src, size_t bytes);
 

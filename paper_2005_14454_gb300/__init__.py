@@ -15,10 +15,12 @@ from __future__ import annotations
 import numpy as np
 
 from . import _abi
-from ._abi import (AHS_FIELD_ALL, AHS_FIELD_E, AHS_FIELD_PHI, AHS_FIELD_PI, AHS_FIELD_THETA,
-                   AHS_MATTER, AHS_MINKOWSKI, AHS_RADIATION, AHSError)
+from ._abi import (AHS_FIELD_ALL, AHS_FIELD_E, AHS_FIELD_LOW, AHS_FIELD_PHI, AHS_FIELD_PI, AHS_FIELD_THETA,
+                   AHS_MATTER, AHS_MINKOWSKI, AHS_PREC_FP32, AHS_PREC_FP32_COMPENSATED, AHS_PREC_FP64,
+                   AHS_RADIATION, AHSError)
 
 ERAS = {"minkowski": AHS_MINKOWSKI, "radiation": AHS_RADIATION, "matter": AHS_MATTER}
+PRECISIONS = {"fp32": _abi.AHS_PREC_FP32, "fp32c": _abi.AHS_PREC_FP32_COMPENSATED, "fp64": _abi.AHS_PREC_FP64}
 
 
 class Lattice:
@@ -26,11 +28,14 @@ class Lattice:
 
     def __init__(self, N: int, dx: float = 0.5, dt: float = 0.1, lambda0: float = 2.0,
                  e0: float = 1.0, sigma: float = 1.0, s: float = 0.0, era=AHS_RADIATION,
-                 measure_every: int = 10, stream: int | None = None):
+                 measure_every: int = 10, stream: int | None = None, precision=None):
         era = ERAS.get(era, era) if isinstance(era, str) else era
         self.N = N
         self.h = _abi.ahs_create(N, dx, dt, lambda0, e0, sigma, s, era)
         _abi.ahs_set_option(self.h, _abi.AHS_OPT_MEASURE_EVERY, measure_every)
+        if precision is not None:
+            precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+            _abi.ahs_set_option(self.h, _abi.AHS_OPT_PRECISION, precision)
         if stream is not None:
             _abi.ahs_set_stream(self.h, stream)
 
@@ -83,7 +88,7 @@ class Lattice:
         return _abi.ahs_fields(self.h, AHS_FIELD_ALL)
 
     def set_state(self, F: np.ndarray):
-        _abi.ahs_set_fields(self.h, AHS_FIELD_ALL, np.ascontiguousarray(F, dtype=np.float32))
+        _abi.ahs_set_fields(self.h, AHS_FIELD_ALL, F)
 
     def field(self, which: int) -> np.ndarray:
         return _abi.ahs_fields(self.h, which)
@@ -151,5 +156,6 @@ class Batch:
         _abi.ahs_batch_autotune(self.b)
 
 
-__all__ = ["Lattice", "Batch", "AHSError", "ERAS", "AHS_FIELD_ALL", "AHS_FIELD_E", "AHS_FIELD_PHI",
-           "AHS_FIELD_PI", "AHS_FIELD_THETA", "AHS_MATTER", "AHS_MINKOWSKI", "AHS_RADIATION"]
+__all__ = ["Lattice", "Batch", "AHSError", "ERAS", "PRECISIONS", "AHS_FIELD_ALL", "AHS_FIELD_E", "AHS_FIELD_LOW",
+           "AHS_FIELD_PHI", "AHS_FIELD_PI", "AHS_FIELD_THETA", "AHS_MATTER", "AHS_MINKOWSKI", "AHS_RADIATION",
+           "AHS_PREC_FP32", "AHS_PREC_FP32_COMPENSATED", "AHS_PREC_FP64"]

@@ -16,10 +16,12 @@ LIB_PATH = os.path.join(_PKG, "_ahs.so")
 
 AHS_OK, AHS_EINVAL, AHS_ENOMEM, AHS_ECUDA, AHS_ESTATE, AHS_ENONFINITE, AHS_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 AHS_MINKOWSKI, AHS_RADIATION, AHS_MATTER = 0, 1, 2
-AHS_FIELD_PHI, AHS_FIELD_PI, AHS_FIELD_THETA, AHS_FIELD_E, AHS_FIELD_ALL = 0, 1, 2, 3, 4
-FIELD_PLANES = {AHS_FIELD_PHI: 2, AHS_FIELD_PI: 2, AHS_FIELD_THETA: 3, AHS_FIELD_E: 3, AHS_FIELD_ALL: 10}
+AHS_FIELD_PHI, AHS_FIELD_PI, AHS_FIELD_THETA, AHS_FIELD_E, AHS_FIELD_ALL, AHS_FIELD_LOW = 0, 1, 2, 3, 4, 5
+FIELD_PLANES = {AHS_FIELD_PHI: 2, AHS_FIELD_PI: 2, AHS_FIELD_THETA: 3, AHS_FIELD_E: 3, AHS_FIELD_ALL: 10,
+                AHS_FIELD_LOW: 5}
+AHS_PREC_FP32, AHS_PREC_FP32_COMPENSATED, AHS_PREC_FP64 = 0, 1, 2
 (AHS_OPT_MEASURE_EVERY, AHS_OPT_ALPHA, AHS_OPT_TAU0, AHS_OPT_STEP, AHS_OPT_WRAP_THETA,
- AHS_OPT_PROFILE, AHS_OPT_N, AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK, AHS_OPT_GRAPH) = range(10)
+ AHS_OPT_PROFILE, AHS_OPT_N, AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK, AHS_OPT_GRAPH, AHS_OPT_PRECISION) = range(11)
 AHS_KERNEL_STEP, AHS_KERNEL_STEP_MEASURE = 0, 1
 
 # every symbol include/ahs.h declares
@@ -171,18 +173,23 @@ def ahs_records(h, max_records: int = 1 << 20):
     return [buf[i].as_dict() for i in range(got)]
 
 
+def storage_dtype(h):
+    return np.float64 if int(ahs_get_option(h, AHS_OPT_PRECISION)) == AHS_PREC_FP64 else np.float32
+
+
 def ahs_fields(h, which, out: np.ndarray | None = None) -> np.ndarray:
     N = int(ahs_get_option(h, AHS_OPT_N))
     shape = (FIELD_PLANES[which], N, N, N)
+    dt = storage_dtype(h)
     if out is None:
-        out = np.empty(shape, dtype=np.float32)
-    assert out.dtype == np.float32 and out.flags.c_contiguous and out.shape == shape
+        out = np.empty(shape, dtype=dt)
+    assert out.dtype == dt and out.flags.c_contiguous and out.shape == shape
     check(lib().ahs_fields(h, which, out.ctypes.data, out.nbytes), "ahs_fields")
     return out
 
 
 def ahs_set_fields(h, which, src: np.ndarray):
-    src = np.ascontiguousarray(src, dtype=np.float32)
+    src = np.ascontiguousarray(src, dtype=storage_dtype(h))
     return check(lib().ahs_set_fields(h, which, src.ctypes.data, src.nbytes), "ahs_set_fields")
 
 

@@ -43,6 +43,7 @@ int ok()
     } while (0)
 
 constexpr int kFields = 10;   // Re phi, Im phi, Re Pi, Im Pi, theta_xyz, E_xyz
+constexpr int kLowPlanes = 5; // compensated precision: low words of Re Pi, Im Pi, E_xyz
 
 }  // namespace
 
@@ -61,7 +62,10 @@ struct ahs : eng::LatticeParams {
     bool ready = false;   // fields defined
     int device = 0;
 
-    float *base = nullptr;           // 2 * kFields planes of V floats
+    int precision = AHS_PREC_FP32;
+    int planes = kFields;            // planes per buffer (15 with low words)
+    size_t esize = sizeof(float);    // bytes per stored value
+    void *base = nullptr;            // 2 buffers of `planes` planes of V values
     double *partials = nullptr;      // nblocks * NQ
     int nblocks = 0;                 // capacity of partials in rows
     int tile_y = 0, zchunk = 0;      // launch-shape overrides (0: automatic)
@@ -75,7 +79,9 @@ struct ahs : eng::LatticeParams {
     double prof_ms[2] = {0.0, 0.0};  // [plain step, measuring step]
     int64_t prof_launches[2] = {0, 0};
 
-    float *plane(int buf, int f) const { return base + ((size_t)buf * kFields + f) * V; }
+    float *plane(int buf, int f) const { return (float *)base + ((size_t)buf * planes + f) * V; }
+    double *plane64(int buf, int f) const { return (double *)base + ((size_t)buf * planes + f) * V; }
+    size_t field_bytes() const { return esize * V * 2 * planes; }
 };
 
 namespace {
@@ -92,7 +98,64 @@ StepPtrs pointers(const ahs_t *h)
     p.qr1 = h->plane(b, 2); p.qi1 = h->plane(b, 3);
     p.tx1 = h->plane(b, 4); p.ty1 = h->plane(b, 5); p.tz1 = h->plane(b, 6);
     p.ex1 = h->plane(b, 7); p.ey1 = h->plane(b, 8); p.ez1 = h->plane(b, 9);
+    const bool lo = h->precision == AHS_PREC_FP32_COMPENSATED;
+    p.qrl = lo ? h->plane(a, 10) : nullptr; p.qil = lo ? h->plane(a, 11) : nullptr;
+    p.exl = lo ? h->plane(a, 12) : nullptr; p.eyl = lo ? h->plane(a, 13) : nullptr;
+    p.ezl = lo ? h->plane(a, 14) : nullptr;
+    p.qrl1 = lo ? h->plane(b, 10) : nullptr; p.qil1 = lo ? h->plane(b, 11) : nullptr;
+    p.exl1 = lo ? h->plane(b, 12) : nullptr; p.eyl1 = lo ? h->plane(b, 13) : nullptr;
+    p.ezl1 = lo ? h->plane(b, 14) : nullptr;
     return p;
+}
+
+StepPtrs64 pointers64(const ahs_t *h)
+{
+    const int a = h->cur, b = 1 - h->cur;
+    StepPtrs64 p;
+    p.pr = h->plane64(a, 0); p.pim = h->plane64(a, 1);
+    p.qr = h->plane64(a, 2); p.qi = h->plane64(a, 3);
+    p.tx = h->plane64(a, 4); p.ty = h->plane64(a, 5); p.tz = h->plane64(a, 6);
+    p.ex = h->plane64(a, 7); p.ey = h->plane64(a, 8); p.ez = h->plane64(a, 9);
+    p.pr1 = h->plane64(b, 0); p.pim1 = h->plane64(b, 1);
+    p.qr1 = h->plane64(b, 2); p.qi1 = h->plane64(b, 3);
+    p.tx1 = h->plane64(b, 4); p.ty1 = h->plane64(b, 5); p.tz1 = h->plane64(b, 6);
+    p.ex1 = h->plane64(b, 7); p.ey1 = h->plane64(b, 8); p.ez1 = h->plane64(b, 9);
+    return p;
+}
+
+// CTAs (rows of partials) of the current step launch
+int launch_blocks(const ahs_t *h)
+{
+    if (h->precision == AHS_PREC_FP64) return step_shape_fp64(h->N).blocks;
+    return step_shape(h->N, h->tile_y, h->zchunk).blocks;
+}
+
+// one step launch (measure: diagnostics into the partials; store: write n+1)
+cudaError_t launch_current(const ahs_t *h, bool measure, bool store)
+{
+    if (h->precision == AHS_PREC_FP64)
+        return launch_step_fp64(pointers64(h), coefficients64(h, h->n), h->N, measure, store, h->partials, h->stream);
+    return launch_step(pointers(h), coefficients(h, h->n), h->N, step_shape(h->N, h->tile_y, h->zchunk), measure, store,
+                       h->partials, h->stream, h->precision == AHS_PREC_FP32_COMPENSATED);
+}
+
+// (re)allocate the field storage for the handle's precision
+int alloc_fields(ahs_t *h)
+{
+    if (h->base) cudaFree(h->base);
+    h->base = nullptr;
+    h->ready = false;
+    h->planes = h->precision == AHS_PREC_FP32_COMPENSATED ? kFields + kLowPlanes : kFields;
+    h->esize = h->precision == AHS_PREC_FP64 ? sizeof(double) : sizeof(float);
+    const size_t bytes = h->field_bytes();
+    cudaError_t e = cudaMalloc(&h->base, bytes);
+    if (e != cudaSuccess) {
+        h->base = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? AHS_ENOMEM : AHS_ECUDA, "cudaMalloc(%zu): %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    return AHS_OK;
 }
 
 // field selector -> (first plane, number of planes)
@@ -104,6 +167,7 @@ bool selector(int which, int *first, int *count)
     case AHS_FIELD_THETA: *first = 4; *count = 3; return true;
     case AHS_FIELD_E: *first = 7; *count = 3; return true;
     case AHS_FIELD_ALL: *first = 0; *count = 10; return true;
+    case AHS_FIELD_LOW: *first = 10; *count = 5; return true;
     default: return false;
     }
 }
@@ -203,16 +267,12 @@ ahs_t *ahs_create(int N, double dx, double dt, double lambda0, double e0, double
         delete h;
         return nullptr;
     }
-    const size_t bytes = sizeof(float) * h->V * 2 * kFields;
-    cudaError_t e = cudaMalloc(&h->base, bytes);
-    if (e != cudaSuccess) {
-        fail(e == cudaErrorMemoryAllocation ? AHS_ENOMEM : AHS_ECUDA, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
-        cudaGetLastError();
+    if (alloc_fields(h) != AHS_OK) {
         delete h;
         return nullptr;
     }
     h->nblocks = step_shape(N, 0, 0).blocks;
-    e = cudaMalloc(&h->partials, sizeof(double) * NQ * (size_t)h->nblocks);
+    cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * NQ * (size_t)h->nblocks);
     if (e != cudaSuccess) {
         fail(AHS_ENOMEM, "cudaMalloc(partials): %s", cudaGetErrorString(e));
         cudaGetLastError();
@@ -254,7 +314,7 @@ int ahs_set_stream(ahs_t *h, void *stream)
 int ahs_device_bytes(ahs_t *h, size_t *bytes)
 {
     if (!h || !bytes) return fail(AHS_EINVAL, "null argument");
-    *bytes = sizeof(float) * h->V * 2 * kFields + sizeof(double) * NQ * (size_t)h->nblocks +
+    *bytes = h->field_bytes() + sizeof(double) * NQ * (size_t)h->nblocks +
              sizeof(ahs_obs_t) * (size_t)h->rec_cap;
     return ok();
 }
@@ -265,8 +325,13 @@ int ahs_init(ahs_t *h, uint64_t seed)
     if (int r = set_device(h)) return r;
     h->cur = 0;
     h->n = 0;
-    CU(cudaMemsetAsync(h->plane(0, 2), 0, sizeof(float) * h->V * 8, h->stream));
-    CU(launch_init(h->plane(0, 0), h->plane(0, 1), h->N, seed, h->sigma, h->stream));
+    if (h->precision == AHS_PREC_FP64) {
+        CU(cudaMemsetAsync(h->plane64(0, 2), 0, sizeof(double) * h->V * (h->planes - 2), h->stream));
+        CU(launch_init_fp64(h->plane64(0, 0), h->plane64(0, 1), h->N, seed, h->sigma, h->stream));
+    } else {
+        CU(cudaMemsetAsync(h->plane(0, 2), 0, sizeof(float) * h->V * (h->planes - 2), h->stream));
+        CU(launch_init(h->plane(0, 0), h->plane(0, 1), h->N, seed, h->sigma, h->stream));
+    }
     CU(cudaStreamSynchronize(h->stream));
     h->ready = true;
     h->log.clear();
@@ -309,6 +374,18 @@ int ahs_set_option(ahs_t *h, int key, double v)
         if (!(v >= 0) || v > h->N || v != std::floor(v)) return fail(AHS_EINVAL, "zchunk must be an integer in [0, N]");
         h->zchunk = (int)v;
         return ok();
+    case AHS_OPT_PRECISION: {
+        if (v != AHS_PREC_FP32 && v != AHS_PREC_FP32_COMPENSATED && v != AHS_PREC_FP64)
+            return fail(AHS_EINVAL, "precision must be AHS_PREC_FP32, _FP32_COMPENSATED or _FP64");
+        if ((int)v == h->precision) return ok();
+        if (int r = set_device(h)) return r;
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        else cudaDeviceSynchronize();
+        h->precision = (int)v;
+        if (int r = alloc_fields(h)) return r;
+        h->cur = 0;
+        return ok();
+    }
     case AHS_OPT_N:
         return fail(AHS_EINVAL, "N is read only");
     default:
@@ -327,6 +404,7 @@ int ahs_get_option(ahs_t *h, int key, double *v)
     case AHS_OPT_WRAP_THETA: *v = h->wrap; break;
     case AHS_OPT_PROFILE: *v = h->profile; break;
     case AHS_OPT_N: *v = h->N; break;
+    case AHS_OPT_PRECISION: *v = h->precision; break;
     case AHS_OPT_TILE_Y: *v = step_shape(h->N, h->tile_y, h->zchunk).by; break;
     case AHS_OPT_ZCHUNK: *v = step_shape(h->N, h->tile_y, h->zchunk).dz; break;
     default: return fail(AHS_EINVAL, "unknown option %d", key);
@@ -346,14 +424,12 @@ int ahs_step(ahs_t *h, int nsteps)
             if ((h->n + i) % h->measure_every == 0) ++nrec;
     }
     if (int r = ensure_records(h, nrec)) return r;
-    if (int r = ensure_partials(h, step_shape(h->N, h->tile_y, h->zchunk).blocks)) return r;
+    if (int r = ensure_partials(h, launch_blocks(h))) return r;
     size_t nev = 0;
     int ri = 0;
     std::vector<char> kind;          // per event pair: 1 if the launch measured
     for (int i = 0; i < nsteps; ++i) {
         const bool meas = h->measure_every > 0 && (h->n % h->measure_every == 0);
-        const StepCoef k = coefficients(h, h->n);
-        const StepPtrs p = pointers(h);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->profile) {
             e0 = event_at(h, nev++);
@@ -362,9 +438,8 @@ int ahs_step(ahs_t *h, int nsteps)
             if (!e0 || !e1) return fail(AHS_ECUDA, "cudaEventCreate failed");
             CU(cudaEventRecord(e0, h->stream));
         }
-        const StepShape sh = step_shape(h->N, h->tile_y, h->zchunk);
-        const int nb = sh.blocks;
-        CU(launch_step(p, k, h->N, sh, meas, true, h->partials, h->stream));
+        const int nb = launch_blocks(h);
+        CU(launch_current(h, meas, true));
         if (h->profile) CU(cudaEventRecord(e1, h->stream));
         if (meas) {
             CU(launch_reduce(h->partials, nb, obs_scalars(h, h->n), h->rec_dev + ri, h->stream));
@@ -397,12 +472,9 @@ int ahs_measure(ahs_t *h, ahs_obs_t *out)
     if (!h || !out) return fail(AHS_EINVAL, "null argument");
     if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
     if (int r = set_device(h)) return r;
-    if (int r = ensure_partials(h, step_shape(h->N, h->tile_y, h->zchunk).blocks)) return r;
-    const StepCoef k = coefficients(h, h->n);
-    const StepPtrs p = pointers(h);
-    const StepShape sh = step_shape(h->N, h->tile_y, h->zchunk);
-    const int nb = sh.blocks;
-    CU(launch_step(p, k, h->N, sh, true, false, h->partials, h->stream));
+    if (int r = ensure_partials(h, launch_blocks(h))) return r;
+    const int nb = launch_blocks(h);
+    CU(launch_current(h, true, false));
     CU(launch_reduce(h->partials, nb, obs_scalars(h, h->n), h->rec_dev, h->stream));
     CU(cudaMemcpyAsync(h->rec_host, h->rec_dev, sizeof(ahs_obs_t), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
@@ -429,14 +501,15 @@ int ahs_fields(ahs_t *h, int which, void *dst, size_t bytes)
 {
     if (!h || !dst) return fail(AHS_EINVAL, "null argument");
     int first, count;
-    if (!selector(which, &first, &count)) return fail(AHS_EINVAL, "unknown field selector %d", which);
-    if (bytes != sizeof(float) * h->V * count)
-        return fail(AHS_EINVAL, "buffer is %zu bytes, field needs %zu", bytes, sizeof(float) * h->V * count);
+    if (!selector(which, &first, &count) || first + count > h->planes)
+        return fail(AHS_EINVAL, "field selector %d not available in this precision", which);
+    const size_t pb = h->esize * h->V;
+    if (bytes != pb * count) return fail(AHS_EINVAL, "buffer is %zu bytes, field needs %zu", bytes, pb * count);
     if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
     if (int r = set_device(h)) return r;
     for (int i = 0; i < count; ++i)
-        CU(cudaMemcpyAsync((float *)dst + (size_t)i * h->V, h->plane(h->cur, first + i), sizeof(float) * h->V,
-                           cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaMemcpyAsync((char *)dst + (size_t)i * pb, (char *)h->base + ((size_t)h->cur * h->planes + first + i) * pb,
+                           pb, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     return ok();
 }
@@ -445,17 +518,23 @@ int ahs_set_fields(ahs_t *h, int which, const void *src, size_t bytes)
 {
     if (!h || !src) return fail(AHS_EINVAL, "null argument");
     int first, count;
-    if (!selector(which, &first, &count)) return fail(AHS_EINVAL, "unknown field selector %d", which);
-    if (bytes != sizeof(float) * h->V * count)
-        return fail(AHS_EINVAL, "buffer is %zu bytes, field needs %zu", bytes, sizeof(float) * h->V * count);
+    if (!selector(which, &first, &count) || first + count > h->planes)
+        return fail(AHS_EINVAL, "field selector %d not available in this precision", which);
+    const size_t pb = h->esize * h->V;
+    if (bytes != pb * count) return fail(AHS_EINVAL, "buffer is %zu bytes, field needs %zu", bytes, pb * count);
     if (int r = set_device(h)) return r;
     if (!h->ready) {
         // a partial set on a fresh handle leaves the other fields zero
-        CU(cudaMemsetAsync(h->plane(h->cur, 0), 0, sizeof(float) * h->V * kFields, h->stream));
+        CU(cudaMemsetAsync((char *)h->base + (size_t)h->cur * h->planes * pb, 0, pb * h->planes, h->stream));
+    } else if (h->precision == AHS_PREC_FP32_COMPENSATED && which != AHS_FIELD_LOW &&
+               (which == AHS_FIELD_PI || which == AHS_FIELD_E || which == AHS_FIELD_ALL)) {
+        // new momenta replace their low words too
+        const int lf = which == AHS_FIELD_E ? 12 : 10, lc = which == AHS_FIELD_PI ? 2 : which == AHS_FIELD_E ? 3 : 5;
+        CU(cudaMemsetAsync((char *)h->base + ((size_t)h->cur * h->planes + lf) * pb, 0, pb * lc, h->stream));
     }
     for (int i = 0; i < count; ++i)
-        CU(cudaMemcpyAsync(h->plane(h->cur, first + i), (const float *)src + (size_t)i * h->V, sizeof(float) * h->V,
-                           cudaMemcpyHostToDevice, h->stream));
+        CU(cudaMemcpyAsync((char *)h->base + ((size_t)h->cur * h->planes + first + i) * pb, (const char *)src + (size_t)i * pb,
+                           pb, cudaMemcpyHostToDevice, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     h->ready = true;
     return ok();
@@ -471,6 +550,7 @@ int ahs_fields_box(ahs_t *h, int which, int x0, int y0, int z0, int nx, int ny, 
     const size_t per = (size_t)nx * ny * nz;
     if (bytes != sizeof(float) * per * count) return fail(AHS_EINVAL, "buffer is %zu bytes, box needs %zu", bytes, sizeof(float) * per * count);
     if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
+    if (h->precision == AHS_PREC_FP64) return fail(AHS_EINVAL, "box copies are float32 only");
     if (int r = set_device(h)) return r;
     auto md = [N](int v) { v %= N; return v < 0 ? v + N : v; };
     const float *planes[10];
@@ -490,6 +570,7 @@ int ahs_windings(ahs_t *h, int8_t *dst, size_t bytes, int64_t *n_wind)
     if (!h || !dst) return fail(AHS_EINVAL, "null argument");
     if (bytes != 3 * h->V) return fail(AHS_EINVAL, "buffer is %zu bytes, windings need %zu", bytes, 3 * h->V);
     if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
+    if (h->precision == AHS_PREC_FP64) return fail(AHS_EINVAL, "the winding field is float32 only (the FP64 measurement counts windings)");
     if (int r = set_device(h)) return r;
     int8_t *W = nullptr;
     CU(cudaMallocAsync(&W, bytes, h->stream));
@@ -512,9 +593,11 @@ int ahs_autotune(ahs_t *h)
 {
     if (!h) return fail(AHS_EINVAL, "null handle");
     if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
+    if (h->precision == AHS_PREC_FP64) return fail(AHS_EINVAL, "the FP64 kernel has a fixed launch shape");
     if (int r = set_device(h)) return r;
     const StepCoef k = coefficients(h, h->n);
     const StepPtrs p = pointers(h);
+    const bool comp = h->precision == AHS_PREC_FP32_COMPENSATED;
     cudaEvent_t e0 = event_at(h, 0), e1 = event_at(h, 1);
     if (!e0 || !e1) return fail(AHS_ECUDA, "cudaEventCreate failed");
     const int bys[2] = {8, 16}, dzs[6] = {4, 8, 16, 32, 64, 128};
@@ -524,11 +607,11 @@ int ahs_autotune(ahs_t *h)
         for (int dz : dzs) {
             if (dz > h->N) continue;
             const StepShape sh = step_shape(h->N, by, dz);
-            CU(launch_step(p, k, h->N, sh, false, true, nullptr, h->stream));   // warm-up
+            CU(launch_step(p, k, h->N, sh, false, true, nullptr, h->stream, comp));   // warm-up
             float tot = 0.f, ms = 0.f;
             for (int rep = 0; rep < 3; ++rep) {
                 CU(cudaEventRecord(e0, h->stream));
-                CU(launch_step(p, k, h->N, sh, false, true, nullptr, h->stream));
+                CU(launch_step(p, k, h->N, sh, false, true, nullptr, h->stream, comp));
                 CU(cudaEventRecord(e1, h->stream));
                 CU(cudaEventSynchronize(e1));
                 CU(cudaEventElapsedTime(&ms, e0, e1));

@@ -97,6 +97,15 @@ static __device__ __forceinline__ int winding(float y1, float y2, float y3, floa
     return __float2int_rn(sum * kInvTwoPiF);
 }
 
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): one step from state v.
+static __device__ __forceinline__ uint64_t splitmix64_device(uint64_t v)
+{
+    uint64_t z = v + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 static __device__ __forceinline__ size_t sidx(int x, int y, int z, int N)
 {
     return (size_t)x + (size_t)N * ((size_t)y + (size_t)N * (size_t)z);

@@ -60,6 +60,31 @@ inline StepCoef coefficients(const LatticeParams *h, int64_t n)
     return k;
 }
 
+inline StepCoef64 coefficients64(const LatticeParams *h, int64_t n)
+{
+    const Scalars S = scalars(h, n);
+    const double dx = h->dx, dt = h->dt;
+    StepCoef64 k;
+    k.cpi = (1.0 - S.delta) / (1.0 + S.delta);
+    k.kpi_lap = dt / ((1.0 + S.delta) * dx * dx);
+    k.kpi_pot = dt * 0.5 * h->lambda0 * S.c / (1.0 + S.delta);
+    k.sigma2 = h->sigma * h->sigma;
+    k.ce = (1.0 - S.omega) / (1.0 + S.omega);
+    k.ke_curl = dt / ((1.0 + S.omega) * dx * dx * dx);
+    k.ke_cur = dt * 2.0 * h->e0 * h->e0 * S.c / ((1.0 + S.omega) * dx);
+    k.dphi = dt;
+    k.dtheta = dt * dx;
+    k.wrap = h->wrap;
+    k.m_grad = 1.0 / (dx * dx);
+    k.m_pot = 0.25 * h->lambda0 * S.c;
+    k.m_el = 1.0 / (2.0 * h->e0 * h->e0 * S.c);
+    k.m_mag = 1.0 / (h->e0 * h->e0 * S.c * dx * dx * dx * dx);
+    const Scalars P = scalars(h, n - 1);
+    k.m_gauss = 2.0 * h->e0 * h->e0 * P.c * (1.0 + P.delta) / (1.0 + P.omega);
+    k.inv_dx = 1.0 / dx;
+    return k;
+}
+
 inline ObsScalars obs_scalars(const LatticeParams *h, int64_t n)
 {
     const Scalars S = scalars(h, n);

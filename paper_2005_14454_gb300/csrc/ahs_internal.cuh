@@ -32,6 +32,15 @@ constexpr int NSUM = 11;   // slots Q_K..Q_G2 are plain sums
 struct StepPtrs {
     const float *pr, *pim, *tx, *ty, *tz, *qr, *qi, *ex, *ey, *ez;
     float *pr1, *pim1, *tx1, *ty1, *tz1, *qr1, *qi1, *ex1, *ey1, *ez1;
+    // compensated precision only: low words of Pi and E (value = high + low)
+    const float *qrl, *qil, *exl, *eyl, *ezl;
+    float *qrl1, *qil1, *exl1, *eyl1, *ezl1;
+};
+
+// FP64 precision mode: the same fields in double
+struct StepPtrs64 {
+    const double *pr, *pim, *tx, *ty, *tz, *qr, *qi, *ex, *ey, *ez;
+    double *pr1, *pim1, *tx1, *ty1, *tz1, *qr1, *qi1, *ex1, *ey1, *ez1;
 };
 
 // Per-step coefficients, computed in FP64 on the host from the step index and
@@ -54,6 +63,15 @@ struct StepCoef {
     float inv_dx;
 };
 
+// the coefficients of StepCoef without rounding, for the FP64 mode
+struct StepCoef64 {
+    double cpi, kpi_lap, kpi_pot, sigma2;
+    double ce, ke_curl, ke_cur;
+    double dphi, dtheta;
+    int wrap;
+    double m_grad, m_pot, m_el, m_mag, m_gauss, inv_dx;
+};
+
 // Scalars the final reduction needs to turn sums into an observable record.
 struct ObsScalars {
     int64_t step;
@@ -69,7 +87,12 @@ struct StepShape {
 };
 StepShape step_shape(int N, int tile_y, int zchunk);   // tile_y/zchunk 0: automatic
 cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, bool measure, bool store,
-                        double *partials, cudaStream_t st);
+                        double *partials, cudaStream_t st, bool compensated = false);
+// FP64 mode (ahs_fp64.cu)
+StepShape step_shape_fp64(int N);
+cudaError_t launch_step_fp64(const StepPtrs64 &p, const StepCoef64 &k, int N, bool measure, bool store,
+                             double *partials, cudaStream_t st);
+cudaError_t launch_init_fp64(double *pr, double *pim, int N, uint64_t seed, double sigma, cudaStream_t st);
 cudaError_t launch_reduce(const double *partials, int nblocks, const ObsScalars &sc,
                           ahs_obs_t *rec, cudaStream_t st);
 cudaError_t launch_windings(const float *pr, const float *pim, const float *tx, const float *ty,

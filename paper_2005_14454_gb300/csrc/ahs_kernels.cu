@@ -12,19 +12,10 @@ namespace eng {
 namespace {
 
 // ---------------------------------------------------------------- init
-// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): one step from state v.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t v)
-{
-    uint64_t z = v + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 __global__ void init_kernel(float *pr, float *pim, size_t V, uint64_t seed, double sigma)
 {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V; i += (size_t)gridDim.x * blockDim.x) {
-        const double u = (double)(splitmix64(seed ^ splitmix64((uint64_t)i)) >> 11) * (1.0 / 9007199254740992.0);
+        const double u = (double)(splitmix64_device(seed ^ splitmix64_device((uint64_t)i)) >> 11) * (1.0 / 9007199254740992.0);
         const double th = __dmul_rn(2.0 * kPiD, u);
         double s, c;
         sincos(th, &s, &c);

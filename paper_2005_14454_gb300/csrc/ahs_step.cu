@@ -61,6 +61,7 @@ struct Raw {
 
 struct PE {
     float qr, qi, ex, ey, ez;
+    float qrl, qil, exl, eyl, ezl;   // low words (compensated precision)
 };
 
 __device__ __forceinline__ int wrapN(int v, int N)
@@ -75,20 +76,22 @@ __device__ __forceinline__ int wrapN(int v, int N)
 // single lattice (kernel parameters, constant bank); ArenaFields addresses the
 // two buffers of one member of a batch from one base pointer with 32-bit plane
 // offsets (requires 20 N^3 < 2^32).
-enum { FPR = 0, FPI, FQR, FQI, FTX, FTY, FTZ, FEX, FEY, FEZ };
+enum { FPR = 0, FPI, FQR, FQI, FTX, FTY, FTZ, FEX, FEY, FEZ, FQRL, FQIL, FEXL, FEYL, FEZL };
 
 struct ParamFields {
     const StepPtrs &P;
     __device__ __forceinline__ float in(int f, uint32_t o) const
     {
         const float *p = f == FPR ? P.pr : f == FPI ? P.pim : f == FQR ? P.qr : f == FQI ? P.qi : f == FTX ? P.tx
-                       : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : P.ez;
+                       : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : f == FEZ ? P.ez
+                       : f == FQRL ? P.qrl : f == FQIL ? P.qil : f == FEXL ? P.exl : f == FEYL ? P.eyl : P.ezl;
         return __ldg(p + o);
     }
     __device__ __forceinline__ void out(int f, uint32_t o, float v) const
     {
         float *p = f == FPR ? P.pr1 : f == FPI ? P.pim1 : f == FQR ? P.qr1 : f == FQI ? P.qi1 : f == FTX ? P.tx1
-                 : f == FTY ? P.ty1 : f == FTZ ? P.tz1 : f == FEX ? P.ex1 : f == FEY ? P.ey1 : P.ez1;
+                 : f == FTY ? P.ty1 : f == FTZ ? P.tz1 : f == FEX ? P.ex1 : f == FEY ? P.ey1 : f == FEZ ? P.ez1
+                 : f == FQRL ? P.qrl1 : f == FQIL ? P.qil1 : f == FEXL ? P.exl1 : f == FEYL ? P.eyl1 : P.ezl1;
         p[o] = v;
     }
 };
@@ -115,7 +118,7 @@ __device__ __forceinline__ Raw load_raw(const FA &P, uint32_t o)
     return a;
 }
 
-template <class FA>
+template <bool COMP, class FA>
 __device__ __forceinline__ PE load_pe(const FA &P, uint32_t o)
 {
     PE a;
@@ -124,7 +127,32 @@ __device__ __forceinline__ PE load_pe(const FA &P, uint32_t o)
     a.ex = P.in(FEX, o);
     a.ey = P.in(FEY, o);
     a.ez = P.in(FEZ, o);
+    if (COMP) {
+        a.qrl = P.in(FQRL, o);
+        a.qil = P.in(FQIL, o);
+        a.exl = P.in(FEXL, o);
+        a.eyl = P.in(FEYL, o);
+        a.ezl = P.in(FEZL, o);
+    } else {
+        a.qrl = a.qil = a.exl = a.eyl = a.ezl = 0.f;
+    }
     return a;
+}
+
+// Compensated damped update of one momentum component held as hi + lo:
+// (hi', lo') = c (hi + lo) + d with the rounding errors of the product c hi (by
+// FMA) and of the sum (TwoSum, Knuth) carried in the low word, then renormalised
+// (Fast2Sum, Dekker).
+__device__ __forceinline__ void comp_update(float c, float hi, float lo, float d, float &nhi, float &nlo)
+{
+    const float p = c * hi;
+    const float e1 = fmaf(c, hi, -p);
+    const float s = p + d;
+    const float bb = s - p;
+    const float e2 = (p - (s - bb)) + (d - bb);
+    const float l = fmaf(c, lo, e1 + e2);
+    nhi = s + l;
+    nlo = l - (nhi - s);
 }
 
 // complex helpers: a * b and a * conj(b)
@@ -148,7 +176,7 @@ __device__ __forceinline__ int next_plane(int z, int N) { return z + 1 == N ? 0 
 // One tile: the 32 x BY column at (x0, y0), planes [z0, zend).  All threads of the
 // CTA call it together (it contains CTA barriers); with MEASURE the CTA's FP64
 // partial sums go to `partial_row`.
-template <int BY, bool MEASURE, bool STORE, class FA>
+template <int BY, bool MEASURE, bool STORE, bool COMP, class FA>
 __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &P, const StepCoef &k, int N,
                                           int x0, int y0, int z0, int zend, double *partial_row)
 {
@@ -233,7 +261,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
             if (hasA) rh = load_raw(P, o2 + haoff);
         }
         pe_cur = pe_next;
-        if (zz + 1 < zend) pe_next = load_pe(P, o1 + coff);
+        if (zz + 1 < zend) pe_next = load_pe<COMP>(P, o1 + coff);
         __syncthreads();
 
         // ---- B: plaquettes of plane zz (tile + backward ring)
@@ -313,8 +341,14 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
             const float hsi = ((hx.y + bxh.y) + (hy.y + byh.y)) + (hz.y + bzh.y);
             const float mod2 = p0.x * p0.x + p0.y * p0.y;
             const float potf = k.kpi_pot * (mod2 - k.sigma2);
-            const float qnr = k.cpi * pe_cur.qr + k.kpi_lap * (hsr - 6.f * p0.x) - potf * p0.x;
-            const float qni = k.cpi * pe_cur.qi + k.kpi_lap * (hsi - 6.f * p0.y) - potf * p0.y;
+            float qnr, qni, qnrl = 0.f, qnil = 0.f;
+            if (COMP) {
+                comp_update(k.cpi, pe_cur.qr, pe_cur.qrl, k.kpi_lap * (hsr - 6.f * p0.x) - potf * p0.x, qnr, qnrl);
+                comp_update(k.cpi, pe_cur.qi, pe_cur.qil, k.kpi_lap * (hsi - 6.f * p0.y) - potf * p0.y, qni, qnil);
+            } else {
+                qnr = k.cpi * pe_cur.qr + k.kpi_lap * (hsr - 6.f * p0.x) - potf * p0.x;
+                qni = k.cpi * pe_cur.qi + k.kpi_lap * (hsi - 6.f * p0.y) - potf * p0.y;
+            }
             // currents J_i = Im(conj(phi) U_i phi(x+i))
             const float jx = p0.x * hx.y - p0.y * hx.x;
             const float jy = p0.x * hy.y - p0.y * hy.x;
@@ -323,19 +357,29 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
             const float cxv = -(sxy - S.sxy[T::q(tx, ty - 1)]) - (sxz - sxzPrev);
             const float cyv = (sxy - S.sxy[T::q(tx - 1, ty)]) - (syz - syzPrev);
             const float czv = (sxz - S.sxz[T::q(tx - 1, ty)]) + (syz - S.syz[T::q(tx, ty - 1)]);
-            const float enx = k.ce * pe_cur.ex + k.ke_curl * cxv + k.ke_cur * jx;
-            const float eny = k.ce * pe_cur.ey + k.ke_curl * cyv + k.ke_cur * jy;
-            const float enz = k.ce * pe_cur.ez + k.ke_curl * czv + k.ke_cur * jz;
+            float enx, eny, enz, enxl = 0.f, enyl = 0.f, enzl = 0.f;
+            if (COMP) {
+                comp_update(k.ce, pe_cur.ex, pe_cur.exl, k.ke_curl * cxv + k.ke_cur * jx, enx, enxl);
+                comp_update(k.ce, pe_cur.ey, pe_cur.eyl, k.ke_curl * cyv + k.ke_cur * jy, eny, enyl);
+                comp_update(k.ce, pe_cur.ez, pe_cur.ezl, k.ke_curl * czv + k.ke_cur * jz, enz, enzl);
+            } else {
+                enx = k.ce * pe_cur.ex + k.ke_curl * cxv + k.ke_cur * jx;
+                eny = k.ce * pe_cur.ey + k.ke_curl * cyv + k.ke_cur * jy;
+                enz = k.ce * pe_cur.ez + k.ke_curl * czv + k.ke_cur * jz;
+            }
 
             if (MEASURE) {
-                const float pbr = 0.5f * (pe_cur.qr + qnr), pbi = 0.5f * (pe_cur.qi + qni);
+                const float pbr = COMP ? 0.5f * ((pe_cur.qr + qnr) + (pe_cur.qrl + qnrl)) : 0.5f * (pe_cur.qr + qnr);
+                const float pbi = COMP ? 0.5f * ((pe_cur.qi + qni) + (pe_cur.qil + qnil)) : 0.5f * (pe_cur.qi + qni);
                 const float K = pbr * pbr + pbi * pbi;
                 const float gxr = hx.x - p0.x, gxi = hx.y - p0.y, gyr = hy.x - p0.x, gyi = hy.y - p0.y;
                 const float gzr = hz.x - p0.x, gzi = hz.y - p0.y;
                 const float G = k.m_grad * ((gxr * gxr + gxi * gxi) + (gyr * gyr + gyi * gyi) + (gzr * gzr + gzi * gzi));
                 const float dm = mod2 - k.sigma2;
                 const float V = k.m_pot * dm * dm;
-                const float ebx = 0.5f * (pe_cur.ex + enx), eby = 0.5f * (pe_cur.ey + eny), ebz = 0.5f * (pe_cur.ez + enz);
+                const float ebx = COMP ? 0.5f * ((pe_cur.ex + enx) + (pe_cur.exl + enxl)) : 0.5f * (pe_cur.ex + enx);
+                const float eby = COMP ? 0.5f * ((pe_cur.ey + eny) + (pe_cur.eyl + enyl)) : 0.5f * (pe_cur.ey + eny);
+                const float ebz = COMP ? 0.5f * ((pe_cur.ez + enz) + (pe_cur.ezl + enzl)) : 0.5f * (pe_cur.ez + enz);
                 const float El = k.m_el * (ebx * ebx + eby * eby + ebz * ebz);
                 const float B = k.m_mag * ((1.f - Qxy.x) + (1.f - Qxz.x) + (1.f - Qyz.x));
                 const float L = K - G - V + El - B;
@@ -374,9 +418,18 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
                 P.out(FEX, o, enx);
                 P.out(FEY, o, eny);
                 P.out(FEZ, o, enz);
-                P.out(FPR, o, p0.x + k.dphi * qnr);
-                P.out(FPI, o, p0.y + k.dphi * qni);
-                float t1x = thx + k.dtheta * enx, t1y = thy + k.dtheta * eny, t1z = thz + k.dtheta * enz;
+                P.out(FPR, o, p0.x + k.dphi * (COMP ? qnr + qnrl : qnr));
+                P.out(FPI, o, p0.y + k.dphi * (COMP ? qni + qnil : qni));
+                if (COMP) {
+                    P.out(FQRL, o, qnrl);
+                    P.out(FQIL, o, qnil);
+                    P.out(FEXL, o, enxl);
+                    P.out(FEYL, o, enyl);
+                    P.out(FEZL, o, enzl);
+                }
+                float t1x = thx + k.dtheta * (COMP ? enx + enxl : enx);
+                float t1y = thy + k.dtheta * (COMP ? eny + enyl : eny);
+                float t1z = thz + k.dtheta * (COMP ? enz + enzl : enz);
                 if (k.wrap) {
                     t1x += kTwoPiF * floorf((kPiF - t1x) * kInvTwoPiF);
                     t1y += kTwoPiF * floorf((kPiF - t1y) * kInvTwoPiF);
@@ -404,7 +457,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
     if (MEASURE) block_reduce_store<32 * BY>(acc, partial_row);
 }
 
-template <int BY, bool MEASURE, bool STORE>
+template <int BY, bool MEASURE, bool STORE, bool COMP>
 __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, int N, int Dz, double *partials)
 {
     using T = Tile<BY>;
@@ -412,8 +465,8 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
     typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
     const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
     const size_t bi = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-    tile_step<BY, MEASURE, STORE>(S, ParamFields{P}, k, N, x0, y0, z0, min(z0 + Dz, N),
-                                  MEASURE ? partials + bi * NQ : nullptr);
+    tile_step<BY, MEASURE, STORE, COMP>(S, ParamFields{P}, k, N, x0, y0, z0, min(z0 + Dz, N),
+                                        MEASURE ? partials + bi * NQ : nullptr);
 }
 
 // Persistent batched step: every CTA claims tiles of the work list one at a time
@@ -446,7 +499,7 @@ __global__ void __launch_bounds__(32 * BY, (MEASURE ? 16 : 24) / BY) batch_step(
         const uint32_t V = (uint32_t)m.N * (uint32_t)m.N * (uint32_t)m.N;
         const ArenaFields fa{m.base, par ? 10u * V : 0u, par ? 0u : 10u * V, V};
         __syncthreads();
-        tile_step<BY, MEASURE, true>(S, fa, sk, m.N, tl.x0, tl.y0, tl.z0, tl.zend,
+        tile_step<BY, MEASURE, true, false>(S, fa, sk, m.N, tl.x0, tl.y0, tl.z0, tl.zend,
                                      MEASURE ? L.partials + (size_t)w * NQ : nullptr);
     }
 }
@@ -478,7 +531,7 @@ cudaError_t launch_batch_variant(const BatchLaunch &L, int dn, int grid, cudaStr
     return cudaGetLastError();
 }
 
-template <int BY, bool M, bool S>
+template <int BY, bool M, bool S, bool C>
 cudaError_t launch_variant(const StepPtrs &p, const StepCoef &k, int N, int Dz, double *partials, cudaStream_t st)
 {
     using T = Tile<BY>;
@@ -488,23 +541,23 @@ cudaError_t launch_variant(const StepPtrs &p, const StepCoef &k, int N, int Dz, 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (configured_device != dev) {
-        e = cudaFuncSetAttribute(step_tiled<BY, M, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        e = cudaFuncSetAttribute(step_tiled<BY, M, S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
         configured_device = dev;
     }
     dim3 block(32, BY);
     dim3 grid((N + 31) / 32, (N + BY - 1) / BY, (N + Dz - 1) / Dz);
-    step_tiled<BY, M, S><<<grid, block, bytes, st>>>(p, k, N, Dz, partials);
+    step_tiled<BY, M, S, C><<<grid, block, bytes, st>>>(p, k, N, Dz, partials);
     return cudaGetLastError();
 }
 
-template <int BY>
+template <int BY, bool C>
 cudaError_t launch_by(const StepPtrs &p, const StepCoef &k, int N, int Dz, bool measure, bool store,
                       double *partials, cudaStream_t st)
 {
-    if (measure && store) return launch_variant<BY, true, true>(p, k, N, Dz, partials, st);
-    if (measure) return launch_variant<BY, true, false>(p, k, N, Dz, partials, st);
-    if (store) return launch_variant<BY, false, true>(p, k, N, Dz, partials, st);
+    if (measure && store) return launch_variant<BY, true, true, C>(p, k, N, Dz, partials, st);
+    if (measure) return launch_variant<BY, true, false, C>(p, k, N, Dz, partials, st);
+    if (store) return launch_variant<BY, false, true, C>(p, k, N, Dz, partials, st);
     return cudaErrorInvalidValue;
 }
 
@@ -539,10 +592,14 @@ cudaError_t launch_batch_step(const BatchLaunch &L, int by, int dn, bool measure
 }
 
 cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, bool measure, bool store,
-                        double *partials, cudaStream_t st)
+                        double *partials, cudaStream_t st, bool compensated)
 {
-    if (sh.by == 16) return launch_by<16>(p, k, N, sh.dz, measure, store, partials, st);
-    return launch_by<8>(p, k, N, sh.dz, measure, store, partials, st);
+    if (compensated) {
+        if (sh.by == 16) return launch_by<16, true>(p, k, N, sh.dz, measure, store, partials, st);
+        return launch_by<8, true>(p, k, N, sh.dz, measure, store, partials, st);
+    }
+    if (sh.by == 16) return launch_by<16, false>(p, k, N, sh.dz, measure, store, partials, st);
+    return launch_by<8, false>(p, k, N, sh.dz, measure, store, partials, st);
 }
 
 }  // namespace eng

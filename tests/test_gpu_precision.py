@@ -1,0 +1,184 @@
+"""Precision modes: FP64 on the GPU against the FP64 oracle (rounding-level
+agreement), compensated float32 momenta against the oracle and against plain
+float32, and checkpoint/resume of the compensated state (high and low words)."""
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = dict(dx=0.5, dt=0.1, lambda0=2.0, e0=1.0, sigma=1.0)
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2005_14454_gb300 as p
+    from paper_2005_14454_gb300 import _abi
+    _abi.lib()
+    return p
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("N,era,s", [(24, 1, 0.0), (20, 2, 1.0), (16, 0, 0.0)])
+def test_fp64_matches_oracle(pkg, orc, N, era, s):
+    with pkg.Lattice(N, era=era, s=s, measure_every=0, precision="fp64", **PARAMS) as lat:
+        lat.init(77)
+        F0 = lat.state()
+        assert F0.dtype == np.float64
+        ref0 = orc.init(orc.Params(N=N, era=era, s=s, **PARAMS), 77)
+        assert np.abs(F0 - ref0).max() < 1e-14
+        lat.step(20)
+        got = lat.state()
+        obs = lat.measure()
+    ref = F0.copy()
+    p = orc.Params(N=N, era=era, s=s, **PARAMS)
+    orc.run(p, 0, 20, ref)
+    for sl in (slice(0, 2), slice(2, 4), slice(4, 7), slice(7, 10)):
+        assert rel(got[sl], ref[sl]) < 1e-11 or np.abs(got[sl] - ref[sl]).max() < 1e-12
+    o = orc.measure(p, 20, got)
+    assert obs["n_wind"] == o["n_wind"]
+    for k in ("e_total", "lagrangian", "v2_phi", "v2_omega", "xi_l", "sum_KL", "sum_pL"):
+        assert obs[k] == pytest.approx(o[k], rel=1e-10), k
+    assert obs["gauss_max"] == pytest.approx(o["gauss_max"], rel=1e-3, abs=1e-12)
+
+
+def test_fp64_minkowski_energy_tracks_oracle(pkg, orc):
+    N, steps = 12, 200
+    F0 = inputs.smooth_state(N, 5, amp=0.1)
+    p = orc.Params(N=N, era=0, **PARAMS)
+    with pkg.Lattice(N, era=0, measure_every=20, precision="fp64", **PARAMS) as lat:
+        lat.set_state(F0)
+        lat.step(steps)
+        recs = lat.records()
+    F = F0.copy()
+    for r in recs:
+        n = r["step"]
+        G = F0.copy()
+        orc.run(p, 0, n, G)
+        o = orc.measure(p, n, G)
+        assert r["e_total"] == pytest.approx(o["e_total"], rel=1e-11)
+
+
+def test_compensated_matches_oracle_and_keeps_low_words(pkg, orc):
+    from paper_2005_14454_gb300 import AHS_FIELD_LOW
+    N, era = 24, 1
+    with pkg.Lattice(N, era=era, measure_every=0, precision="fp32c", **PARAMS) as lat:
+        lat.init(9)
+        F0 = lat.state().astype(np.float64)
+        lat.step(10)
+        hi = lat.state().astype(np.float64)
+        lo = lat.field(AHS_FIELD_LOW).astype(np.float64)
+    assert np.abs(lo).max() > 0.0
+    assert np.abs(lo[0:2]).max() <= 1e-6 * np.abs(hi[2:4]).max()
+    got = hi.copy()
+    got[2:4] += lo[0:2]
+    got[7:10] += lo[2:5]
+    ref = F0.copy()
+    orc.run(orc.Params(N=N, era=era, **PARAMS), 0, 10, ref)
+    for sl in (slice(0, 2), slice(2, 4), slice(7, 10)):
+        assert rel(got[sl], ref[sl]) < 1e-5
+
+
+def test_compensated_not_worse_than_fp32_over_a_long_run(pkg, orc):
+    N, steps = 16, 300
+    F0 = inputs.to_f32(inputs.smooth_state(N, 3, amp=0.1)).astype(np.float64)
+    p = orc.Params(N=N, era=0, **PARAMS)
+    ref = F0.copy()
+    orc.run(p, 0, steps, ref)
+    errs = {}
+    from paper_2005_14454_gb300 import AHS_FIELD_LOW
+    for prec in ("fp32", "fp32c"):
+        with pkg.Lattice(N, era=0, measure_every=0, precision=prec, **PARAMS) as lat:
+            lat.set_state(F0)
+            lat.step(steps)
+            got = lat.state().astype(np.float64)
+            if prec == "fp32c":
+                lo = lat.field(AHS_FIELD_LOW).astype(np.float64)
+                got[2:4] += lo[0:2]
+                got[7:10] += lo[2:5]
+        errs[prec] = max(rel(got[sl], ref[sl]) for sl in (slice(0, 2), slice(2, 4), slice(7, 10)))
+    assert errs["fp32"] < 1e-4
+    assert errs["fp32c"] <= 1.5 * errs["fp32"], errs
+
+
+def test_compensated_resume_is_bit_exact(pkg):
+    from paper_2005_14454_gb300 import AHS_FIELD_LOW
+    N = 20
+    with pkg.Lattice(N, measure_every=0, precision="fp32c", **PARAMS) as a:
+        a.init(4)
+        a.step(12)
+        full, full_lo = a.state(), a.field(AHS_FIELD_LOW)
+    with pkg.Lattice(N, measure_every=0, precision="fp32c", **PARAMS) as b:
+        b.init(4)
+        b.step(6)
+        snap, snap_lo = b.state(), b.field(AHS_FIELD_LOW)
+    from paper_2005_14454_gb300 import _abi
+    with pkg.Lattice(N, measure_every=0, precision="fp32c", **PARAMS) as c:
+        c.set_state(snap)
+        _abi.ahs_set_fields(c.h, AHS_FIELD_LOW, snap_lo)
+        c.n = 6
+        c.step(6)
+        assert np.array_equal(c.state(), full)
+        assert np.array_equal(c.field(AHS_FIELD_LOW), full_lo)
+
+
+def test_precision_option_rules(pkg):
+    from paper_2005_14454_gb300 import AHSError, AHS_FIELD_LOW, _abi
+    with pkg.Lattice(8, measure_every=0, **PARAMS) as lat:
+        lat.init(1)
+        with pytest.raises(AHSError):
+            lat.field(AHS_FIELD_LOW)                  # no low words in plain float32
+        lat.set_option(_abi.AHS_OPT_PRECISION, _abi.AHS_PREC_FP64)
+        with pytest.raises(AHSError):
+            lat.step(1)                               # changing precision discards the fields
+        lat.init(1)
+        lat.step(2)
+        with pytest.raises(AHSError):
+            lat.windings()
+        with pytest.raises(AHSError):
+            lat.set_option(_abi.AHS_OPT_PRECISION, 7)
+
+
+def test_precision_study_small_lattice_against_oracle(pkg, orc):
+    """The precision study of the Minkowski random-phase run on 32^3 for 2000 steps:
+    energy drift and Gauss residual of each mode next to the oracle's.  FP64 tracks
+    the oracle's energy to rounding until chaos amplifies the last-bit differences
+    of two FP64 implementations (~600 steps); every mode's energy drift matches the
+    oracle's (it is the O(dt^2) oscillation of the integrator, not rounding)."""
+    from paper_2005_14454_gb300 import AHS_FIELD_LOW
+    N, steps, every = 32, 2000, 200
+    p = orc.Params(N=N, era=0, **PARAMS)
+    starts = {}
+    with pkg.Lattice(N, era=0, measure_every=0, **PARAMS) as lat:
+        lat.init(1)
+        starts["f32"] = lat.state().astype(np.float64)
+    starts["f64"] = orc.init(p, 1)
+    ref = {}
+    for key, F0 in starts.items():
+        F = F0.copy()
+        e = [orc.measure(p, 0, F)["e_total"]]
+        for n in range(0, steps, every):
+            orc.run(p, n, every, F)
+            e.append(orc.measure(p, n + every, F)["e_total"])
+        ref[key] = (np.array(e), orc.gauss(p, steps, F)[1])
+    drift = {}
+    for mode in ("fp32", "fp32c", "fp64"):
+        with pkg.Lattice(N, era=0, measure_every=every, precision=mode, **PARAMS) as lat:
+            lat.init(1)
+            lat.step(steps)
+            recs = lat.records() + [lat.measure()]
+        e = np.array([r["e_total"] for r in recs])
+        key = "f64" if mode == "fp64" else "f32"
+        drift[mode] = np.abs(e - e[0]).max() / e[0]
+        oracle_drift = np.abs(ref[key][0] - ref[key][0][0]).max() / ref[key][0][0]
+        assert abs(drift[mode] - oracle_drift) < 0.02 * oracle_drift + 1e-4
+        if mode == "fp64":
+            assert np.allclose(e[:4], ref[key][0][:4], rtol=1e-9)
+            assert recs[-1]["gauss_rms"] < 1e-11
+        else:
+            assert recs[-1]["gauss_rms"] < 1e-4
+    print("energy drift", drift)
