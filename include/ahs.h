@@ -78,7 +78,9 @@ enum {
     AHS_OPT_TILE_Y = 7,        /* step-kernel tile height: 8 or 16 rows of 32 sites; 0 = auto   */
     AHS_OPT_ZCHUNK = 8,        /* z planes one CTA marches through, 1..N; 0 = auto            */
     AHS_OPT_GRAPH = 9,         /* batches: 1 = replay each measurement period as a CUDA graph  */
-    AHS_OPT_PRECISION = 10     /* AHS_PREC_*; default FP32                                     */
+    AHS_OPT_PRECISION = 10,    /* AHS_PREC_*; default FP32                                     */
+    AHS_OPT_COOLING = 11       /* > 0: cooling steps, a = 1 and delta = omega = value (the
+                                  artificial damping period Sec. 2 mentions); 0 = off       */
 };
 
 typedef struct ahs ahs_t;

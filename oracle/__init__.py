@@ -49,7 +49,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("e0", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("s", ctypes.c_double), ("era", ctypes.c_int),
-                ("alpha", ctypes.c_double), ("tau0", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("tau0", ctypes.c_double), ("cool", ctypes.c_double)]
 
 
 class _Obs(ctypes.Structure):
@@ -109,7 +109,7 @@ class Params:
     """Run parameters (Sec. 2): lattice side N, spacing dx, time step dt, couplings
     lambda0, e0, vev sigma, width exponent s (lambda, e scale so a^{2s} multiplies
     the potential and the current), era p (a = (eta/eta0)^p), damping form alpha,
-    initial conformal time tau0."""
+    initial conformal time tau0, cooling damping cool (> 0: a = 1, delta = omega = cool)."""
     N: int
     dx: float = 0.5
     dt: float = 0.1
@@ -120,10 +120,11 @@ class Params:
     era: int = 1
     alpha: float = 2.0
     tau0: float = 1.0
+    cool: float = 0.0
 
     def c(self) -> _Params:
         return _Params(self.N, self.dx, self.dt, self.lambda0, self.e0, self.sigma,
-                       self.s, self.era, self.alpha, self.tau0)
+                       self.s, self.era, self.alpha, self.tau0, self.cool)
 
 
 def zeros(N: int) -> np.ndarray:

@@ -39,6 +39,7 @@ typedef struct {
     int era;        /* conformal expansion exponent p: a = (eta/eta0)^p */
     double alpha;   /* damping form factor of Eq. 11, 2 in the paper  */
     double tau0;    /* initial conformal time eta0, 1 in the paper     */
+    double cool;    /* > 0: cooling run, a = 1 and delta = omega = cool (see orc_scalars) */
 } orc_params_t;
 
 typedef struct {
@@ -87,6 +88,14 @@ void orc_scalars(const orc_params_t *p, int64_t n, double out[5])
     double delta = 0.5 * p->alpha * (double)p->era * p->dt / eta;
     double omega = delta * (1.0 - p->s);
     double c = pow(a, 2.0 * p->s);
+    /* Cooling (the artificial damping period Sec. 2 mentions without details):
+     * read as a static background, a = 1, with the same constant Crank-Nicolson
+     * damping on both momenta, delta = omega = cool. */
+    if (p->cool > 0.0) {
+        a = 1.0;
+        delta = omega = p->cool;
+        c = 1.0;
+    }
     out[0] = eta; out[1] = a; out[2] = delta; out[3] = omega; out[4] = c;
 }
 

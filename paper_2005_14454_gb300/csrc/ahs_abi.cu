@@ -386,6 +386,10 @@ int ahs_set_option(ahs_t *h, int key, double v)
         h->cur = 0;
         return ok();
     }
+    case AHS_OPT_COOLING:
+        if (!(v >= 0) || !std::isfinite(v) || v >= 1.0) return fail(AHS_EINVAL, "cooling damping must be in [0, 1)");
+        h->cooling = v;
+        return ok();
     case AHS_OPT_N:
         return fail(AHS_EINVAL, "N is read only");
     default:
@@ -405,6 +409,7 @@ int ahs_get_option(ahs_t *h, int key, double *v)
     case AHS_OPT_PROFILE: *v = h->profile; break;
     case AHS_OPT_N: *v = h->N; break;
     case AHS_OPT_PRECISION: *v = h->precision; break;
+    case AHS_OPT_COOLING: *v = h->cooling; break;
     case AHS_OPT_TILE_Y: *v = step_shape(h->N, h->tile_y, h->zchunk).by; break;
     case AHS_OPT_ZCHUNK: *v = step_shape(h->N, h->tile_y, h->zchunk).dz; break;
     default: return fail(AHS_EINVAL, "unknown option %d", key);

@@ -565,6 +565,11 @@ int ahs_batch_set_option(ahs_batch_t *b, int key, double v)
         if (v != 0 && v != 1) return bfail(AHS_EINVAL, "profile must be 0 or 1");
         b->profile = (int)v;
         return report_ok();
+    case AHS_OPT_COOLING:
+        if (!(v >= 0) || !std::isfinite(v) || v >= 1.0) return bfail(AHS_EINVAL, "cooling damping must be in [0, 1)");
+        for (auto &p : b->prm) p.cooling = v;
+        b->tables_dirty = true;
+        return report_ok();
     case AHS_OPT_TILE_Y:
         if (v != 8 && v != 16) return bfail(AHS_EINVAL, "tile_y must be 8 or 16");
         b->by = (int)v;
@@ -595,6 +600,7 @@ int ahs_batch_get_option(ahs_batch_t *b, int key, double *v)
     case AHS_OPT_TAU0: *v = b->prm[0].tau0; break;
     case AHS_OPT_WRAP_THETA: *v = b->prm[0].wrap; break;
     case AHS_OPT_PROFILE: *v = b->profile; break;
+    case AHS_OPT_COOLING: *v = b->prm[0].cooling; break;
     case AHS_OPT_TILE_Y: *v = b->by; break;
     case AHS_OPT_GRAPH: *v = b->use_graph; break;
     case AHS_OPT_STEP: *v = (double)b->n; break;

@@ -16,6 +16,7 @@ struct LatticeParams {
     int era = 1;
     double alpha = 2.0, tau0 = 1.0;
     int wrap = 0;
+    double cooling = 0.0;   // > 0: cooling run, a = 1 and delta = omega = cooling
 };
 
 // FP64 scalars of step n (Eqs. 7, 8, 11, 12): eta, a, delta, omega, c = a^{2s}
@@ -31,6 +32,13 @@ inline Scalars scalars(const LatticeParams *h, int64_t n)
     r.delta = 0.5 * h->alpha * (double)h->era * h->dt / r.eta;
     r.omega = r.delta * (1.0 - h->s);
     r.c = std::pow(r.a, 2.0 * h->s);
+    if (h->cooling > 0.0) {
+        // cooling (the artificial damping period of Sec. 2): static background with
+        // the same constant Crank-Nicolson damping on both momenta
+        r.a = 1.0;
+        r.delta = r.omega = h->cooling;
+        r.c = 1.0;
+    }
     return r;
 }
 

@@ -310,3 +310,29 @@ def test_full_size_sampled_sites(eng, orc):
         orc.run(p, 3, 1, ref)
         r = ref[:, 2, 2, 2]
         assert np.allclose(A, r, rtol=2e-6, atol=2e-6), (A, r)
+
+
+# ------------------------------------------------------------------ cooling, straight strings
+def test_cooled_vortex_pair_matches_oracle(eng, orc):
+    """Straight vortex-antivortex pair along z relaxed by 200 cooling steps (a = 1,
+    delta = omega = 0.5): windings exactly +-1 at the cores on every z-layer and
+    2N in total at every measurement, fields equal to the oracle's."""
+    from paper_2005_14454_gb300._abi import AHS_OPT_COOLING
+    N = 32
+    F0 = inputs.to_f32(inputs.with_phase(inputs.vortex_pair_phase(N))).astype(np.float64)
+    with lattice(eng, N, measure_every=20) as lat:
+        lat.set_option(AHS_OPT_COOLING, 0.5)
+        lat.set_state(F0)
+        lat.step(200)
+        recs = lat.records()
+        got = lat.state().astype(np.float64)
+        W, n = lat.windings()
+    assert [r["n_wind"] for r in recs] == [2 * N] * 10
+    e = [r["e_total"] for r in recs]
+    assert all(b < a for a, b in zip(e, e[1:]))
+    (x1, y1), (x2, y2) = inputs.vortex_pair_cores(N)
+    assert n == 2 * N and (W[0, :, y1, x1] == 1).all() and (W[0, :, y2, x2] == -1).all()
+    ref = F0.copy()
+    orc.run(oparams(orc, N, cool=0.5), 0, 200, ref)
+    err = field_errors(got, ref)
+    assert max(err.values()) < 1e-5, err

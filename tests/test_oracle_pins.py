@@ -415,3 +415,35 @@ def test_measure_closed_form_twisted_state(orc):
     L = K - G + El
     assert o["lagrangian"] == pytest.approx(dx ** 3 * N ** 3 * L, rel=1e-12)
     assert o["xi_l"] == pytest.approx(math.sqrt(-2 * math.pi * sig ** 2 * (N * dx) ** 3 / o["lagrangian"]), rel=1e-12)
+
+
+# --------------------------------------------------------------------------- cooling
+def test_cooling_relaxes_vortex_pair_and_keeps_windings(orc):
+    # cooling: a = 1, delta = omega = 0.5 (the damping period of Sec. 2, reading
+    # of the design notes).  Dissipative: the energy falls; topological: the two
+    # hand-placed straight strings keep winding +-1 on every z-layer; Gauss's law
+    # stays exact (delta = omega, c = 1).  At critical coupling (beta = lambda0 /
+    # 2 e0^2 = 1) the relaxed straight string is the BPS vortex, whose energy per
+    # unit length is 2 pi sigma^2 -- the tension used in xi_L.
+    N = 24
+    p = P(orc, N, era=1, cool=0.5)
+    sc = orc.scalars(p, 37)
+    assert sc["a"] == 1.0 and sc["delta"] == 0.5 and sc["omega"] == 0.5 and sc["c"] == 1.0
+    F = inputs.with_phase(inputs.vortex_pair_phase(N))
+    e0 = orc.measure(p, 0, F)["e_total"]
+    last = e0
+    for n in range(0, 200, 20):
+        orc.run(p, n, 20, F)
+        o = orc.measure(p, n + 20, F)
+        assert o["n_wind"] == 2 * N
+        assert o["e_total"] < last
+        assert o["gauss_max"] < 1e-12
+        last = o["e_total"]
+    W, _ = orc.windings(p, F)
+    (x1, y1), (x2, y2) = inputs.vortex_pair_cores(N)
+    assert (W[0, :, y1, x1] == 1).all() and (W[0, :, y2, x2] == -1).all()
+    tension = last / (2 * N * p.dx)                       # two strings of length N dx
+    assert tension == pytest.approx(2 * math.pi * p.sigma ** 2, rel=0.03)
+    # relaxed cores: |phi| dips towards the strings and approaches sigma far away
+    mod = np.hypot(F[0], F[1])
+    assert mod[:, y1, x1].max() < 0.6 and mod[:, 0, 0].min() > 0.99
