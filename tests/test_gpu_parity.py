@@ -335,4 +335,8 @@ def test_cooled_vortex_pair_matches_oracle(eng, orc):
     ref = F0.copy()
     orc.run(oparams(orc, N, cool=0.5), 0, 200, ref)
     err = field_errors(got, ref)
-    assert max(err.values()) < 1e-5, err
+    assert err["phi"] < 1e-5 and err["theta"] < 1e-5, err
+    # the momenta are damped towards zero: compare them on the scale of phi
+    scale = np.linalg.norm(ref[0:2])
+    assert np.linalg.norm(got[2:4] - ref[2:4]) / scale < 1e-5
+    assert np.linalg.norm(got[7:10] - ref[7:10]) / scale < 1e-5
