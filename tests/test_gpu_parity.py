@@ -131,6 +131,27 @@ def test_perturbed_state_with_gauge_fields(eng, orc):
     assert max(err.values()) < 1e-5, err
 
 
+@pytest.mark.parametrize("span", [3.0, 50.0, 9000.0])
+def test_large_link_angles(eng, orc, span):
+    # link angles over many turns, up to the large-argument range of the float32
+    # sine and cosine: one step against the oracle
+    N = 16
+    F = inputs.perturbed_state(N, 31)
+    rng = np.random.default_rng(5)
+    F[4:7] = rng.uniform(-span, span, (3, N, N, N))
+    F0 = inputs.to_f32(F).astype(np.float64)
+    with lattice(eng, N) as lat:
+        lat.set_state(F0)
+        lat.step(1)
+        got = lat.state().astype(np.float64)
+    ref = F0.copy()
+    orc.run(oparams(orc, N), 0, 1, ref)
+    # theta itself carries float32 rounding of its magnitude: compare the kicks
+    for sl in (slice(0, 2), slice(2, 4), slice(7, 10)):
+        assert rel(got[sl], ref[sl]) < 2e-6 * max(1.0, span / 50.0)
+    assert np.abs(got[4:7] - ref[4:7]).max() < 4e-7 * span + 1e-6
+
+
 def test_vacuum_is_exact_fixed_point(eng):
     N = 16
     F = np.zeros((10, N, N, N), np.float32)
