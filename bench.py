@@ -48,6 +48,53 @@ def dist_env():
     return ws, rank, local
 
 
+class Group:
+    """The replicas of a multi-GPU run, one process per GPU, each advancing its own
+    realisation (no collective on the data path): a barrier around the timed
+    region and the maximum of the per-rank times.  Single process: no-ops.
+    backend "nccl" on the GPU run, "gloo" for CPU tests of the same logic."""
+
+    def __init__(self, backend: str = "nccl", device=None):
+        import torch
+        self.torch = torch
+        self.ws, self.rank, self.local = dist_env()
+        self.dist = None
+        self.device = device if device is not None else ("cuda" if backend == "nccl" else "cpu")
+        if self.ws > 1:
+            import torch.distributed as dist
+            kw = {"device_id": torch.device("cuda", self.local)} if backend == "nccl" else {}
+            dist.init_process_group(backend, **kw)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.device == "cuda":
+            self.torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return float(x)
+        t = self.torch.tensor([float(x)], dtype=self.torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def replica_seed(rank: int) -> int:
+    """Seed of the realisation a rank advances (distinct per rank)."""
+    return 1000 + rank
+
+
+def aggregate_rate(ws: int, sites_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job site-updates per second: all ranks' work over the slowest rank's time."""
+    return ws * sites_per_rank * steps / seconds
+
+
 # --------------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -270,10 +317,7 @@ def run_ours(args, N):
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    group = Group("nccl")
 
     from paper_2005_14454_gb300 import _abi
     stream = torch.cuda.current_stream()
@@ -283,14 +327,11 @@ def run_ours(args, N):
     _abi.ahs_set_option(h, _abi.AHS_OPT_MEASURE_EVERY, PERIOD)
     _abi.ahs_set_option(h, _abi.AHS_OPT_TILE_Y, args.tile_y)
     _abi.ahs_set_option(h, _abi.AHS_OPT_ZCHUNK, args.zchunk)
-    _abi.ahs_init(h, 1000 + rank)
+    _abi.ahs_init(h, replica_seed(rank))
     shape = {"tile": [32, int(_abi.ahs_get_option(h, _abi.AHS_OPT_TILE_Y))],
              "zchunk": int(_abi.ahs_get_option(h, _abi.AHS_OPT_ZCHUNK))}
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
+    barrier = group.barrier
 
     for _ in range(args.warmup):
         _abi.ahs_step(h, PERIOD)
@@ -333,12 +374,8 @@ def run_ours(args, N):
             rec_bytes += len(_abi.ahs_records(h)) * _abi.lib().ahs_sizeof_obs()
         _abi.check(_abi.lib().ahs_fields(h, _abi.AHS_FIELD_ALL, host.data_ptr(), state_bytes), "ahs_fields")
         barrier()
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": ws * N ** 3 * PERIOD * args.steps / e2e_s, "unit": "site-updates/s",
+        e2e_s = group.max(time.perf_counter() - t0)
+        e2e = {"value": aggregate_rate(ws, N ** 3, PERIOD * args.steps, e2e_s), "unit": "site-updates/s",
                "h2d_bytes_per_step": state_bytes / args.steps,
                "d2h_bytes_per_step": (state_bytes + rec_bytes) / args.steps,
                "note": "state uploaded from pinned host memory once, records read back every step, "
@@ -347,16 +384,12 @@ def run_ours(args, N):
 
     _abi.ahs_destroy(h)
 
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = group.max(ms)
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
+        group.close()
         return 0
 
-    value = ws * N ** 3 * PERIOD * args.steps / (ms / 1e3)
+    value = aggregate_rate(ws, N ** 3, PERIOD * args.steps, ms / 1e3)
     pk, pk_kind = peaks()
     avg_ms = k_ms / max(k_n, 1)
     bytes_per_launch = BYTES_PER_SITE * N ** 3
@@ -382,8 +415,7 @@ def run_ours(args, N):
         line["ensemble"] = run_ensemble(torch)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
-    if dist is not None:
-        dist.destroy_process_group()
+    group.close()
     print(json.dumps(line), flush=True)
     return 0
 
