@@ -1,6 +1,16 @@
 """Studies run on the engine (one GPU).
 
   python -m paper_2005_14454_gb300.study precision [--size 512] [--steps 2000] [--box 48]
+  python -m paper_2005_14454_gb300.study table1 [--size 1024] [--eras 1 2] [--seeds 1-20] [--every 5]
+  python -m paper_2005_14454_gb300.study table1-summary FILE...
+
+table1: the scaling runs of Sec. 4 (Table 1): random-phase starts evolved with constant
+comoving width (s = 0) to half a light-crossing time, diagnostics every `every` steps;
+per run the slopes of xi_L(tau) and xi_W(tau) from a least-squares line over the fit
+range (Table 1's [100.5, 255.5] at 1024^3, scaled with the box otherwise) and the means
+of <v^2>_omega and <v^2>_phi over the same range; then the mean and the sample standard
+deviation over the realisations of each era.  One JSON object per run and per era.
+table1-summary aggregates the run lines of earlier invocations.
 
 precision: the same Minkowski run (a = 1, no damping; lambda0 = 2, e0 = 1, sigma = 1,
 dx = 0.5, dt = 0.1, random-phase start) in the three precision modes -- float32,
@@ -86,6 +96,86 @@ def precision(args):
         print(json.dumps(res), flush=True)
 
 
+def fit_rate(tau, xi, lo, hi):
+    """Slope of the least-squares line through (tau, xi) over lo <= tau <= hi
+    (finite points only); NaN with fewer than three points."""
+    tau, xi = np.asarray(tau, float), np.asarray(xi, float)
+    m = (tau >= lo) & (tau <= hi) & np.isfinite(xi)
+    if m.sum() < 3:
+        return float("nan")
+    t = tau[m] - tau[m].mean()
+    return float(np.dot(t, xi[m] - xi[m].mean()) / np.dot(t, t))
+
+
+def fit_range(N, dx=0.5, tau0=1.0):
+    """Table 1's fit range [100.5, 255.5] of the 1024^3, dx = 0.5 runs (end of run at
+    tau = 256), scaled to the end of a run on N^3."""
+    end = 0.5 * dx * N
+    return 100.5 / 256.0 * end, 255.5 / 256.0 * end
+
+
+def table1_run(N, era, seed, every, lo, hi, chunk=250):
+    """One realisation: (per-run summary, series of tau, xi_L, xi_W, v2_omega, v2_phi)."""
+    steps = int(round((0.5 * PARAMS["dx"] * N - 1.0) / PARAMS["dt"]))
+    recs = []
+    t0 = time.perf_counter()
+    with Lattice(N, era=era, measure_every=every, **PARAMS) as lat:
+        lat.init(seed)
+        done = 0
+        while done <= steps:
+            k = min(chunk, steps + 1 - done)
+            lat.step(k)
+            done += k
+            recs += lat.records()
+    secs = time.perf_counter() - t0
+    ser = {k: np.array([r[k] for r in recs], float) for k in ("tau", "xi_l", "xi_w", "v2_omega", "v2_phi")}
+    m = (ser["tau"] >= lo) & (ser["tau"] <= hi)
+    out = {"study": "table1", "N": N, "era": era, "seed": seed, "steps": steps, "every": every,
+           "fit": [lo, hi], "points": int(m.sum()),
+           "xi_dot_L": fit_rate(ser["tau"], ser["xi_l"], lo, hi),
+           "xi_dot_W": fit_rate(ser["tau"], ser["xi_w"], lo, hi),
+           "v2_omega": float(np.mean(ser["v2_omega"][m])), "v2_phi": float(np.mean(ser["v2_phi"][m])),
+           "xi_w_end": float(ser["xi_w"][-1]), "xi_l_end": float(ser["xi_l"][-1]),
+           "n_wind_end": int(recs[-1]["n_wind"]), "seconds": secs}
+    return out, ser
+
+
+TABLE1_KEYS = ("xi_dot_L", "xi_dot_W", "v2_omega", "v2_phi")
+
+
+def table1_summary(runs):
+    """Mean and sample standard deviation over realisations, per (N, era)."""
+    groups = {}
+    for r in runs:
+        groups.setdefault((r["N"], r["era"]), []).append(r)
+    out = []
+    for (N, era), rs in sorted(groups.items()):
+        d = {"study": "table1-summary", "N": N, "era": era, "runs": len(rs),
+             "seeds": sorted(r["seed"] for r in rs)}
+        for k in TABLE1_KEYS:
+            v = np.array([r[k] for r in rs], float)
+            d[k] = [float(v.mean()), float(v.std(ddof=1)) if v.size > 1 else float("nan")]
+        out.append(d)
+    return out
+
+
+def _seeds(spec):
+    a, _, b = spec.partition("-")
+    return list(range(int(a), int(b or a) + 1))
+
+
+def table1(args):
+    lo, hi = args.fit if args.fit else fit_range(args.size)
+    runs = []
+    for seed in _seeds(args.seeds):
+        for era in args.eras:
+            r, _ = table1_run(args.size, era, seed, args.every, lo, hi)
+            runs.append(r)
+            print(json.dumps(r), flush=True)
+    for d in table1_summary(runs):
+        print(json.dumps(d), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(prog="python -m paper_2005_14454_gb300.study")
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -95,9 +185,30 @@ def main(argv=None):
     pp.add_argument("--box", type=int, default=48)
     pp.add_argument("--measure-every", type=int, default=100)
     pp.add_argument("--seed", type=int, default=1)
+    tp = sub.add_parser("table1")
+    tp.add_argument("--size", type=int, default=1024)
+    tp.add_argument("--eras", type=int, nargs="+", default=[1, 2])
+    tp.add_argument("--seeds", default="1-20", help="first-last realisation seed")
+    tp.add_argument("--every", type=int, default=5)
+    tp.add_argument("--fit", type=float, nargs=2, default=None, help="fit range in tau")
+    sp = sub.add_parser("table1-summary")
+    sp.add_argument("files", nargs="+")
     args = ap.parse_args(argv)
     if args.cmd == "precision":
         precision(args)
+    elif args.cmd == "table1":
+        table1(args)
+    elif args.cmd == "table1-summary":
+        runs = []
+        for f in args.files:
+            for line in open(f):
+                line = line.strip()
+                if line.startswith("{"):
+                    d = json.loads(line)
+                    if d.get("study") == "table1":
+                        runs.append(d)
+        for d in table1_summary(runs):
+            print(json.dumps(d), flush=True)
     return 0
 
 
