@@ -16,6 +16,44 @@ constexpr double kPiD = 3.141592653589793238;
 // is recomputed in FP64 with the operations in the order of the definition.
 constexpr float kTie = 1e-4f;
 
+// ---------------------------------------------------------------- link phases
+// (cos th, sin th) of a link angle (Eq. 13) without the library sincosf: th is
+// reduced to r = th - k pi, |r| <= pi/2, k = rint(th / pi), with pi split into two
+// float32 parts (Cody & Waite, "Software Manual for the Elementary Functions",
+// 1980) so that the fused multiply-adds leave r accurate to about an ulp for
+// |th| up to ~1e5; then sin r = r + r^3 S(r^2) and cos r = 1 + r^2 C(r^2) with the
+// near-minimax polynomials of gen_link_sincos.py (degrees 9 and 10), and both
+// change sign for odd k.  Error: at most 1.3e-7 (sin) and 1.5e-7 (cos) absolute,
+// i.e. 1-2 ulp of values near 1; |V|^2 - 1 is unbiased to 4e-9.  No branches and
+// no special-function unit: 17 instructions on the FMA and ALU pipes.
+constexpr float kLinkS0 = -0.16666659712791443f, kLinkS1 = 0.00833306647837162f,
+                kLinkS2 = -0.0001980959059437737f, kLinkS3 = 2.605750751172309e-06f;
+constexpr float kLinkC0 = -0.5f, kLinkC1 = 0.04166664183139801f, kLinkC2 = -0.00138884037733078f,
+                kLinkC3 = 2.476187000866048e-05f, kLinkC4 = -2.607681608424173e-07f;
+constexpr float kLinkInvPi = 0.31830987334251404f;   // float32(1/pi)
+constexpr float kLinkPiA = 3.1415927410125732f;      // float32(pi)
+constexpr float kLinkPiB = -8.742277657347586e-08f;  // float32(pi - kLinkPiA)
+
+static __device__ __forceinline__ void link_sincos(float th, float &s, float &c)
+{
+    const float k = rintf(th * kLinkInvPi);
+    float r = fmaf(-k, kLinkPiA, th);
+    r = fmaf(-k, kLinkPiB, r);
+    const float r2 = r * r;
+    float ps = fmaf(r2, kLinkS3, kLinkS2);
+    ps = fmaf(r2, ps, kLinkS1);
+    ps = fmaf(r2, ps, kLinkS0);
+    float pc = fmaf(r2, kLinkC4, kLinkC3);
+    pc = fmaf(r2, pc, kLinkC2);
+    pc = fmaf(r2, pc, kLinkC1);
+    pc = fmaf(r2, pc, kLinkC0);
+    const float sv = fmaf(r * r2, ps, r);
+    const float cv = fmaf(r2, pc, 1.0f);
+    const unsigned flip = (unsigned)__float2int_rn(k) << 31;   // (-1)^k as a sign bit
+    s = __uint_as_float(__float_as_uint(sv) ^ flip);
+    c = __uint_as_float(__float_as_uint(cv) ^ flip);
+}
+
 // ---------------------------------------------------------------- windings
 // Y_i(x) = arg(phi^*(x) U_i(x) phi(x+i)), U_i = exp(-i theta_i).
 static __device__ __noinline__ double link_phase_fp64(float pr, float pi, float qr, float qi, float th)

@@ -30,7 +30,7 @@ __global__ void init_kernel(float *pr, float *pim, size_t V, uint64_t seed, doub
 __device__ __forceinline__ float2 vphase(float th)
 {
     float s, c;
-    sincosf(th, &s, &c);
+    link_sincos(th, s, c);
     return make_float2(c, s);
 }
 

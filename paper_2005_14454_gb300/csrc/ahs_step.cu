@@ -18,6 +18,10 @@
 // Values a site needs from its z-1 neighbour (phi, V_z, sin alpha_xz/yz, E_z) are
 // carried in registers from the previous plane; in-plane neighbours come from
 // shared memory.  Every link phase and plaquette of the tile is computed once.
+// Two CTA barriers per plane (after A and after B): the link phases rotate
+// through three plane buffers, so phase A of plane z+1 never writes a buffer
+// that a thread still in phase C of plane z-1 reads, and the barrier after A
+// orders every other shared array (each is written in B and read in C).
 // Tile coordinates wrap modulo N, so ragged tiles and N < 32 need no special path.
 // Site offsets are 32-bit (the handle limits N^3 below 2^32).
 #include "ahs_device.cuh"
@@ -41,7 +45,7 @@ struct Tile {
         float2 vx[NR], vy[NR], vz[NR], ph[NR];
     };
     struct Smem {
-        Plane pl[2];
+        Plane pl[3];
         float sxy[NS], sxz[NS], syz[NS];
         // measurement steps only
         float yx[NYW], yy[NYW], yz[NYW];
@@ -213,11 +217,11 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
 
     auto phaseA = [&](const Raw &a, int ri, typename T::Plane &pl) {
         float s, c;
-        sincosf(a.tx, &s, &c);
+        link_sincos(a.tx, s, c);
         pl.vx[ri] = make_float2(c, s);
-        sincosf(a.ty, &s, &c);
+        link_sincos(a.ty, s, c);
         pl.vy[ri] = make_float2(c, s);
-        sincosf(a.tz, &s, &c);
+        link_sincos(a.tz, s, c);
         pl.vz[ri] = make_float2(c, s);
         pl.ph[ri] = make_float2(a.pr, a.pi);
     };
@@ -249,8 +253,9 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
 
     int b = 0;   // plane buffer holding plane zz
     for (int zz = z0 - 1; zz < zend; ++zz) {
+        const int bn = b == 2 ? 0 : b + 1;   // third buffer: see the barrier note at the top
         typename T::Plane &pc = S.pl[b];
-        typename T::Plane &pn = S.pl[b ^ 1];
+        typename T::Plane &pn = S.pl[bn];
         const uint32_t oc = (uint32_t)zc * NN, o1 = (uint32_t)z1 * NN, o2 = (uint32_t)z2 * NN;
         // ---- A: link phases and phi of plane zz+1
         phaseA(rc, T::r(tx, ty), pn);
@@ -450,8 +455,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
         YyCar = YyNext;
         thx = nthx; thy = nthy; thz = nthz;
         zc = z1; z1 = z2; z2 = next_plane(z2, N);
-        b ^= 1;
-        __syncthreads();
+        b = bn;
     }
 
     if (MEASURE) block_reduce_store<32 * BY>(acc, partial_row);
