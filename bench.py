@@ -33,12 +33,15 @@ PARAMS = dict(dx=0.5, dt=0.1, lambda0=2.0, e0=1.0, sigma=1.0, s=0.0)
 ERA = 1                         # radiation
 
 
-def workload(N):
-    return {"workload": f"abelian-higgs leapfrog {N}^3 fp32, radiation era, s=0, lambda0=2, e0=1, "
-                        f"sigma=1, dx=0.5, dt=0.1, random-phase init, diagnostics fused every {PERIOD} steps",
-            "lattice": N, "leapfrog_steps_per_step": PERIOD, "era": "radiation", "s": 0.0,
-            "l2": "inputs larger than L2 (state %.1f GB resident in HBM)" % (N ** 3 * BYTES_PER_SITE / 1e9),
-            "parallelism": "replicas (one lattice per GPU)"}
+def workload(N, inplace=False):
+    d = {"workload": f"abelian-higgs leapfrog {N}^3 fp32, radiation era, s=0, lambda0=2, e0=1, "
+                     f"sigma=1, dx=0.5, dt=0.1, random-phase init, diagnostics fused every {PERIOD} steps",
+         "lattice": N, "leapfrog_steps_per_step": PERIOD, "era": "radiation", "s": 0.0,
+         "l2": "inputs larger than L2 (state %.1f GB resident in HBM)" % (N ** 3 * BYTES_PER_SITE / 1e9),
+         "parallelism": "replicas (one lattice per GPU)"}
+    if inplace:
+        d["storage"] = "Pi and E updated in place (60 B/site allocated); measuring steps as two launches"
+    return d
 
 
 def dist_env():
@@ -324,6 +327,8 @@ def run_ours(args, N):
     h = _abi.ahs_create(N, PARAMS["dx"], PARAMS["dt"], PARAMS["lambda0"], PARAMS["e0"], PARAMS["sigma"],
                         PARAMS["s"], ERA)
     _abi.ahs_set_stream(h, stream.cuda_stream)
+    if args.momenta_in_place:
+        _abi.ahs_set_option(h, _abi.AHS_OPT_MOMENTA_IN_PLACE, 1)
     _abi.ahs_set_option(h, _abi.AHS_OPT_MEASURE_EVERY, PERIOD)
     _abi.ahs_set_option(h, _abi.AHS_OPT_TILE_Y, args.tile_y)
     _abi.ahs_set_option(h, _abi.AHS_OPT_ZCHUNK, args.zchunk)
@@ -399,14 +404,16 @@ def run_ours(args, N):
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": workload(N),
+        "data": "synthetic", "config": workload(N, args.momenta_in_place),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
                      "kernel": "step_tiled (plain leapfrog step)", "peak_kind": pk_kind,
                      "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                      "launches": k_n, "measure_kernel_avg_ms": km_ms / max(km_n, 1),
                      "launch_shape": shape},
-        "gpu_launches": args.steps * (PERIOD + 1),
+        # per period: PERIOD step launches (+1 measurement launch with in-place
+        # momenta) and one reduction
+        "gpu_launches": args.steps * (PERIOD + (2 if args.momenta_in_place else 1)),
         "clocks": clocks.summary(),
         "e2e": e2e,
         "nonfinite": nonfinite,
@@ -433,6 +440,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--momenta-in-place", action="store_true",
+                    help="store Pi and E once (60 B/site; lattices up to 1600^3)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warm-up must be at least 3 steps", file=sys.stderr)

@@ -79,9 +79,21 @@ enum {
     AHS_OPT_ZCHUNK = 8,        /* z planes one CTA marches through, 1..N; 0 = auto            */
     AHS_OPT_GRAPH = 9,         /* batches: 1 = replay each measurement period as a CUDA graph  */
     AHS_OPT_PRECISION = 10,    /* AHS_PREC_*; default FP32                                     */
-    AHS_OPT_COOLING = 11       /* > 0: cooling steps, a = 1 and delta = omega = value (the
+    AHS_OPT_COOLING = 11,      /* > 0: cooling steps, a = 1 and delta = omega = value (the
                                   artificial damping period Sec. 2 mentions); 0 = off       */
+    AHS_OPT_MOMENTA_IN_PLACE = 12 /* 1: keep one copy of Pi and E and update it in place  */
 };
+
+/* AHS_OPT_MOMENTA_IN_PLACE (float32 precision only; changing it discards the
+ * fields).  The kicks of Eqs. 7-8 give each site's new Pi and E from its own old
+ * values, so Pi and E need no second buffer; phi and theta, which the stencil
+ * reads at neighbours, stay double-buffered.  Device storage drops from 80 to 60
+ * bytes per site (a 1536^3 lattice takes 217 GB).  The fields, records and the
+ * results of every call are bit-identical to the default storage.  Costs: a
+ * measuring step runs as two launches (the measurement, then the step), because
+ * its Gauss residual reads the old E of neighbouring sites that the fused step
+ * would overwrite; ahs_autotune returns AHS_ESTATE (it times real steps, which
+ * would advance the momenta). */
 
 typedef struct ahs ahs_t;
 

@@ -28,7 +28,8 @@ class Lattice:
 
     def __init__(self, N: int, dx: float = 0.5, dt: float = 0.1, lambda0: float = 2.0,
                  e0: float = 1.0, sigma: float = 1.0, s: float = 0.0, era=AHS_RADIATION,
-                 measure_every: int = 10, stream: int | None = None, precision=None):
+                 measure_every: int = 10, stream: int | None = None, precision=None,
+                 momenta_in_place: bool = False):
         era = ERAS.get(era, era) if isinstance(era, str) else era
         self.N = N
         self.h = _abi.ahs_create(N, dx, dt, lambda0, e0, sigma, s, era)
@@ -36,6 +37,8 @@ class Lattice:
         if precision is not None:
             precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
             _abi.ahs_set_option(self.h, _abi.AHS_OPT_PRECISION, precision)
+        if momenta_in_place:
+            _abi.ahs_set_option(self.h, _abi.AHS_OPT_MOMENTA_IN_PLACE, 1)
         if stream is not None:
             _abi.ahs_set_stream(self.h, stream)
 

@@ -65,7 +65,9 @@ struct ahs : eng::LatticeParams {
     int precision = AHS_PREC_FP32;
     int planes = kFields;            // planes per buffer (15 with low words)
     size_t esize = sizeof(float);    // bytes per stored value
-    void *base = nullptr;            // 2 buffers of `planes` planes of V values
+    int inplace = 0;                 // Pi and E stored once (AHS_OPT_MOMENTA_IN_PLACE)
+    void *base = nullptr;            // 2 buffers of `planes` planes of V values; in place:
+                                     // buffer 0 (10 planes), then phi and theta of buffer 1
     double *partials = nullptr;      // nblocks * NQ
     int nblocks = 0;                 // capacity of partials in rows
     int tile_y = 0, zchunk = 0;      // launch-shape overrides (0: automatic)
@@ -79,9 +81,18 @@ struct ahs : eng::LatticeParams {
     double prof_ms[2] = {0.0, 0.0};  // [plain step, measuring step]
     int64_t prof_launches[2] = {0, 0};
 
-    float *plane(int buf, int f) const { return (float *)base + ((size_t)buf * planes + f) * V; }
-    double *plane64(int buf, int f) const { return (double *)base + ((size_t)buf * planes + f) * V; }
-    size_t field_bytes() const { return esize * V * 2 * planes; }
+    // index of plane f of buffer buf in the allocation
+    size_t plane_index(int buf, int f) const
+    {
+        if (!inplace || buf == 0) return (size_t)buf * planes + f;
+        if (f < 2) return kFields + f;                 // phi of buffer 1
+        if (f >= 4 && f < 7) return kFields + f - 2;   // theta of buffer 1
+        return f;                                      // Pi, E: the single copy
+    }
+    size_t total_planes() const { return inplace ? kFields + 5 : 2 * (size_t)planes; }
+    float *plane(int buf, int f) const { return (float *)base + plane_index(buf, f) * V; }
+    double *plane64(int buf, int f) const { return (double *)base + plane_index(buf, f) * V; }
+    size_t field_bytes() const { return esize * V * total_planes(); }
 };
 
 namespace {
@@ -378,6 +389,7 @@ int ahs_set_option(ahs_t *h, int key, double v)
         if (v != AHS_PREC_FP32 && v != AHS_PREC_FP32_COMPENSATED && v != AHS_PREC_FP64)
             return fail(AHS_EINVAL, "precision must be AHS_PREC_FP32, _FP32_COMPENSATED or _FP64");
         if ((int)v == h->precision) return ok();
+        if (h->inplace && v != AHS_PREC_FP32) return fail(AHS_EINVAL, "in-place momenta need float32 precision");
         if (int r = set_device(h)) return r;
         if (h->stream) cudaStreamSynchronize(h->stream);
         else cudaDeviceSynchronize();
@@ -390,6 +402,18 @@ int ahs_set_option(ahs_t *h, int key, double v)
         if (!(v >= 0) || !std::isfinite(v) || v >= 1.0) return fail(AHS_EINVAL, "cooling damping must be in [0, 1)");
         h->cooling = v;
         return ok();
+    case AHS_OPT_MOMENTA_IN_PLACE: {
+        if (v != 0 && v != 1) return fail(AHS_EINVAL, "momenta_in_place must be 0 or 1");
+        if ((int)v == h->inplace) return ok();
+        if (v == 1 && h->precision != AHS_PREC_FP32) return fail(AHS_EINVAL, "in-place momenta need float32 precision");
+        if (int r = set_device(h)) return r;
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        else cudaDeviceSynchronize();
+        h->inplace = (int)v;
+        if (int r = alloc_fields(h)) return r;
+        h->cur = 0;
+        return ok();
+    }
     case AHS_OPT_N:
         return fail(AHS_EINVAL, "N is read only");
     default:
@@ -410,6 +434,7 @@ int ahs_get_option(ahs_t *h, int key, double *v)
     case AHS_OPT_N: *v = h->N; break;
     case AHS_OPT_PRECISION: *v = h->precision; break;
     case AHS_OPT_COOLING: *v = h->cooling; break;
+    case AHS_OPT_MOMENTA_IN_PLACE: *v = h->inplace; break;
     case AHS_OPT_TILE_Y: *v = step_shape(h->N, h->tile_y, h->zchunk).by; break;
     case AHS_OPT_ZCHUNK: *v = step_shape(h->N, h->tile_y, h->zchunk).dz; break;
     default: return fail(AHS_EINVAL, "unknown option %d", key);
@@ -444,7 +469,14 @@ int ahs_step(ahs_t *h, int nsteps)
             CU(cudaEventRecord(e0, h->stream));
         }
         const int nb = launch_blocks(h);
-        CU(launch_current(h, meas, true));
+        if (meas && h->inplace) {
+            // the Gauss residual reads neighbours' old E, which an in-place step
+            // overwrites: measure first, then step
+            CU(launch_current(h, true, false));
+            CU(launch_current(h, false, true));
+        } else {
+            CU(launch_current(h, meas, true));
+        }
         if (h->profile) CU(cudaEventRecord(e1, h->stream));
         if (meas) {
             CU(launch_reduce(h->partials, nb, obs_scalars(h, h->n), h->rec_dev + ri, h->stream));
@@ -513,7 +545,7 @@ int ahs_fields(ahs_t *h, int which, void *dst, size_t bytes)
     if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
     if (int r = set_device(h)) return r;
     for (int i = 0; i < count; ++i)
-        CU(cudaMemcpyAsync((char *)dst + (size_t)i * pb, (char *)h->base + ((size_t)h->cur * h->planes + first + i) * pb,
+        CU(cudaMemcpyAsync((char *)dst + (size_t)i * pb, (char *)h->base + h->plane_index(h->cur, first + i) * pb,
                            pb, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     return ok();
@@ -530,15 +562,16 @@ int ahs_set_fields(ahs_t *h, int which, const void *src, size_t bytes)
     if (int r = set_device(h)) return r;
     if (!h->ready) {
         // a partial set on a fresh handle leaves the other fields zero
-        CU(cudaMemsetAsync((char *)h->base + (size_t)h->cur * h->planes * pb, 0, pb * h->planes, h->stream));
+        for (int f = 0; f < h->planes; ++f)
+            CU(cudaMemsetAsync((char *)h->base + h->plane_index(h->cur, f) * pb, 0, pb, h->stream));
     } else if (h->precision == AHS_PREC_FP32_COMPENSATED && which != AHS_FIELD_LOW &&
                (which == AHS_FIELD_PI || which == AHS_FIELD_E || which == AHS_FIELD_ALL)) {
         // new momenta replace their low words too
         const int lf = which == AHS_FIELD_E ? 12 : 10, lc = which == AHS_FIELD_PI ? 2 : which == AHS_FIELD_E ? 3 : 5;
-        CU(cudaMemsetAsync((char *)h->base + ((size_t)h->cur * h->planes + lf) * pb, 0, pb * lc, h->stream));
+        CU(cudaMemsetAsync((char *)h->base + h->plane_index(h->cur, lf) * pb, 0, pb * lc, h->stream));
     }
     for (int i = 0; i < count; ++i)
-        CU(cudaMemcpyAsync((char *)h->base + ((size_t)h->cur * h->planes + first + i) * pb, (const char *)src + (size_t)i * pb,
+        CU(cudaMemcpyAsync((char *)h->base + h->plane_index(h->cur, first + i) * pb, (const char *)src + (size_t)i * pb,
                            pb, cudaMemcpyHostToDevice, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     h->ready = true;
@@ -599,6 +632,7 @@ int ahs_autotune(ahs_t *h)
     if (!h) return fail(AHS_EINVAL, "null handle");
     if (!h->ready) return fail(AHS_ESTATE, "fields not initialised");
     if (h->precision == AHS_PREC_FP64) return fail(AHS_EINVAL, "the FP64 kernel has a fixed launch shape");
+    if (h->inplace) return fail(AHS_ESTATE, "autotuning times real steps, which would advance in-place momenta");
     if (int r = set_device(h)) return r;
     const StepCoef k = coefficients(h, h->n);
     const StepPtrs p = pointers(h);

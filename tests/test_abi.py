@@ -75,3 +75,14 @@ def test_null_handle_is_rejected(abi):
 def test_binding_raises_without_library(tmp_path, abi):
     with pytest.raises(ImportError):
         abi.load(str(tmp_path / "missing.so"))
+
+
+def test_binding_constants_match_the_header(abi):
+    txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ahs.h")).read(), flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"\b(AHS_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt)}
+    assert len(consts) > 30
+    for name, value in consts.items():
+        if name == "AHS_NOALLOC_MAX_ROWS":
+            continue
+        assert getattr(abi, name) == value, name
+    assert consts["AHS_OPT_MOMENTA_IN_PLACE"] == 12
