@@ -49,7 +49,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
                 ("lambda0", ctypes.c_double), ("e0", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("s", ctypes.c_double), ("era", ctypes.c_int),
-                ("alpha", ctypes.c_double), ("tau0", ctypes.c_double), ("cool", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("tau0", ctypes.c_double), ("cool", ctypes.c_double),
+                ("s_cg", ctypes.c_double), ("tau_cg", ctypes.c_double)]
 
 
 class _Obs(ctypes.Structure):
@@ -109,7 +110,8 @@ class Params:
     """Run parameters (Sec. 2): lattice side N, spacing dx, time step dt, couplings
     lambda0, e0, vev sigma, width exponent s (lambda, e scale so a^{2s} multiplies
     the potential and the current), era p (a = (eta/eta0)^p), damping form alpha,
-    initial conformal time tau0, cooling damping cool (> 0: a = 1, delta = omega = cool)."""
+    initial conformal time tau0, cooling damping cool (> 0: a = 1, delta = omega = cool),
+    core growth: the steps with eta < tau_cg use s_cg in place of s."""
     N: int
     dx: float = 0.5
     dt: float = 0.1
@@ -121,10 +123,12 @@ class Params:
     alpha: float = 2.0
     tau0: float = 1.0
     cool: float = 0.0
+    s_cg: float = 0.0
+    tau_cg: float = 0.0
 
     def c(self) -> _Params:
         return _Params(self.N, self.dx, self.dt, self.lambda0, self.e0, self.sigma,
-                       self.s, self.era, self.alpha, self.tau0, self.cool)
+                       self.s, self.era, self.alpha, self.tau0, self.cool, self.s_cg, self.tau_cg)
 
 
 def zeros(N: int) -> np.ndarray:

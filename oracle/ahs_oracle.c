@@ -40,6 +40,8 @@ typedef struct {
     double alpha;   /* damping form factor of Eq. 11, 2 in the paper  */
     double tau0;    /* initial conformal time eta0, 1 in the paper     */
     double cool;    /* > 0: cooling run, a = 1 and delta = omega = cool (see orc_scalars) */
+    double s_cg;    /* core growth: s of the steps with eta < tau_cg (see orc_scalars)  */
+    double tau_cg;  /* end of the core-growth period; <= tau0: none                   */
 } orc_params_t;
 
 typedef struct {
@@ -86,8 +88,22 @@ void orc_scalars(const orc_params_t *p, int64_t n, double out[5])
     double eta = p->tau0 + (double)n * p->dt;
     double a = pow(eta / p->tau0, (double)p->era);
     double delta = 0.5 * p->alpha * (double)p->era * p->dt / eta;
-    double omega = delta * (1.0 - p->s);
-    double c = pow(a, 2.0 * p->s);
+    /* Core growth (Sec. 2, after Eq. 6): a negative s lets the comoving string
+     * width grow before the true equations (s = 1) shrink it again.  Read as the
+     * exponent s_cg for the steps with eta < tau_cg and s after them, in omega and
+     * in c, with c continuous at tau_cg (the couplings change their rate of
+     * change, they do not jump): c = a^{2 s_cg} before, a_cg^{2 s_cg} (a/a_cg)^{2 s}
+     * after, a_cg = a(tau_cg).  tau_cg <= tau0: constant s. */
+    int grow = p->tau_cg > p->tau0;
+    double s = grow && eta < p->tau_cg ? p->s_cg : p->s;
+    double omega = delta * (1.0 - s);
+    double c;
+    if (grow && eta >= p->tau_cg) {
+        double acg = pow(p->tau_cg / p->tau0, (double)p->era);
+        c = pow(acg, 2.0 * p->s_cg) * pow(a / acg, 2.0 * p->s);
+    } else {
+        c = pow(a, 2.0 * s);
+    }
     /* Cooling (the artificial damping period Sec. 2 mentions without details):
      * read as a static background, a = 1, with the same constant Crank-Nicolson
      * damping on both momenta, delta = omega = cool. */

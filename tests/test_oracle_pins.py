@@ -447,3 +447,97 @@ def test_cooling_relaxes_vortex_pair_and_keeps_windings(orc):
     # relaxed cores: |phi| dips towards the strings and approaches sigma far away
     mod = np.hypot(F[0], F[1])
     assert mod[:, y1, x1].max() < 0.6 and mod[:, 0, 0].min() > 0.99
+
+
+# --------------------------------------------------------------------------- core growth
+def test_core_growth_scalars(orc):
+    # steps with eta < tau_cg use s_cg in omega and c = a^{2 s_cg}; later steps s,
+    # with c continuous at tau_cg: c = a_cg^{2 s_cg} (a / a_cg)^{2 s}
+    p = P(orc, 8, era=1, s=1.0, s_cg=-1.0, tau_cg=3.05)
+    before, after = orc.scalars(p, 15), orc.scalars(p, 30)       # eta = 2.5, 4.0
+    assert before["c"] == pytest.approx(2.5 ** -2) and before["omega"] == pytest.approx(2 * before["delta"])
+    assert after["omega"] == 0.0 and after["c"] == pytest.approx(3.05 ** -2 * (4.0 / 3.05) ** 2)
+    # continuity across the switch (steps 20 and 21 straddle eta = 3.05)
+    c20, c21 = orc.scalars(p, 20)["c"], orc.scalars(p, 21)["c"]
+    assert abs(c21 / c20 - 1) < 0.1
+    # no period (tau_cg <= tau0) and s_cg = s both give the constant-s scalars
+    q = P(orc, 8, era=2, s=1.0)
+    for r in (P(orc, 8, era=2, s=1.0, s_cg=-1.0, tau_cg=1.0), P(orc, 8, era=2, s=1.0, s_cg=1.0, tau_cg=5.0)):
+        for n in (0, 7, 45, 80):
+            a, b = orc.scalars(q, n), orc.scalars(r, n)
+            assert b["omega"] == a["omega"] and b["c"] == pytest.approx(a["c"], rel=1e-14)
+
+
+def test_core_growth_before_the_switch_is_the_constant_s_run(orc):
+    N = 6
+    F = inputs.perturbed_state(N, seed=4)
+    sched = P(orc, N, era=1, s=1.0, s_cg=-1.0, tau_cg=2.05)     # steps 0..10 have eta < 2.05
+    const = P(orc, N, era=1, s=-1.0)
+    A, B = F.copy(), F.copy()
+    orc.run(sched, 0, 11, A)
+    orc.run(const, 0, 11, B)
+    assert np.array_equal(A, B)
+    orc.run(sched, 11, 3, A)
+    orc.run(const, 11, 3, B)
+    assert not np.array_equal(A, B)
+    off = P(orc, N, era=1, s=1.0, s_cg=-1.0, tau_cg=0.5)
+    C, D = F.copy(), F.copy()
+    orc.run(off, 0, 14, C)
+    orc.run(P(orc, N, era=1, s=1.0), 0, 14, D)
+    assert np.array_equal(C, D)
+
+
+def test_core_growth_keeps_strings_resolved(orc):
+    """Why the period exists (Sec. 2): a relaxed straight vortex pair evolved in the
+    radiation era with the true equations (s = 1) shrinks below the lattice spacing
+    and its windings are lost by eta = 3; with a core-growth period (s = -1 until
+    eta = 3, then s = 1) the cores first widen, then shrink, and both strings still
+    wind on every layer at eta = 8.  After the switch s = 1 keeps the Gauss residual
+    exactly (radiation), so it stays constant."""
+    N = 24
+    F = inputs.with_phase(inputs.vortex_pair_phase(N))
+    orc.run(P(orc, N, era=1, cool=0.5), 0, 200, F)
+
+    def core_sites(G):
+        return int((G[0] ** 2 + G[1] ** 2 < 0.5 * 1.0 ** 2).sum())
+
+    a0 = core_sites(F)
+    plain = F.copy()
+    p1 = P(orc, N, era=1, s=1.0)
+    orc.run(p1, 0, 20, plain)
+    assert orc.measure(p1, 20, plain)["n_wind"] == 0
+    grow = F.copy()
+    pg = P(orc, N, era=1, s=1.0, s_cg=-1.0, tau_cg=3.05)
+    areas, gauss = {}, {}
+    n = 0
+    for stop in (20, 50, 70):
+        orc.run(pg, n, stop - n, grow)
+        n = stop
+        o = orc.measure(pg, n, grow)
+        areas[n], gauss[n] = core_sites(grow), o["gauss_max"]
+        assert o["n_wind"] == 2 * N, n
+    assert areas[20] >= 2 * a0 and areas[50] > areas[20] and areas[70] < areas[50]
+    assert abs(gauss[70] - gauss[50]) < 1e-9
+
+
+def test_stable_time_step_bound(orc):
+    """Leapfrog stability (reading G13): dt * omega_max < 2 with omega_max^2 =
+    12/dx^2 + max(lambda0, 2 e0^2) sigma^2 c_max.  The matter era with s = 1 at
+    dt = 0.1 breaks the bound near eta = 3.6 and the oracle's energy blows up
+    before eta = 5; at the step the bound gives for eta_end = 5 the same start
+    stays finite to the end."""
+    from paper_2005_14454_gb300 import stable_dt
+    dt = stable_dt(dx=0.5, lambda0=2.0, e0=1.0, sigma=1.0, s=1.0, era=2, tau_end=5.0)
+    assert dt == pytest.approx(0.9 * 2 / math.sqrt(48 + 2 * 5.0 ** 4))
+    for step, finite in ((0.1, False), (dt, True)):
+        p = P(orc, 8, era=2, s=1.0, dt=step)
+        F = orc.init(p, 3)
+        steps = int(round(4.0 / step))
+        orc.run(p, 0, steps, F)
+        e = orc.measure(p, steps, F)["e_total"]
+        assert bool(np.isfinite(e) and abs(e) < 1e4) == finite
+    # constant-width runs (s = 0) are bounded by the lattice term alone
+    assert stable_dt(0.5, 2.0, 1.0, 1.0, 0.0, 1, 256.0) == pytest.approx(0.9 * 2 / math.sqrt(48 + 2))
+    # core growth: c peaks at the end of the run, below the constant-s = 1 value
+    assert stable_dt(0.5, 2.0, 1.0, 1.0, 1.0, 1, 16.0, s_cg=-1.0, tau_cg=4.0) > \
+        stable_dt(0.5, 2.0, 1.0, 1.0, 1.0, 1, 16.0)
