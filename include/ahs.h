@@ -81,8 +81,19 @@ enum {
     AHS_OPT_PRECISION = 10,    /* AHS_PREC_*; default FP32                                     */
     AHS_OPT_COOLING = 11,      /* > 0: cooling steps, a = 1 and delta = omega = value (the
                                   artificial damping period Sec. 2 mentions); 0 = off       */
-    AHS_OPT_MOMENTA_IN_PLACE = 12 /* 1: keep one copy of Pi and E and update it in place  */
+    AHS_OPT_MOMENTA_IN_PLACE = 12, /* 1: keep one copy of Pi and E and update it in place */
+    AHS_OPT_CORE_GROWTH_S = 13,   /* s of the core-growth period (see below); default 0    */
+    AHS_OPT_CORE_GROWTH_TAU = 14  /* end eta_cg of the period; <= eta0 (default): none     */
 };
+
+/* Core growth (Sec. 2, after Eq. 6): a negative s makes the comoving string width
+ * grow, so that the true equations (s = 1) can later shrink it without it falling
+ * below the lattice spacing.  Steps with eta_n < AHS_OPT_CORE_GROWTH_TAU use the
+ * exponent s_cg = AHS_OPT_CORE_GROWTH_S in omega = delta (1 - s) and c = a^{2 s};
+ * later steps use the s of ahs_create, with c kept continuous at eta_cg:
+ * c = a_cg^{2 s_cg} (a / a_cg)^{2 s}, a_cg = a(eta_cg).  (The paper gives no
+ * switching rule; a jump of c would quench the string cores.)  Gauss's law is
+ * kept exactly only where constant s keeps it (see ahs_obs_t.gauss_rms). */
 
 /* AHS_OPT_MOMENTA_IN_PLACE (float32 precision only; changing it discards the
  * fields).  The kicks of Eqs. 7-8 give each site's new Pi and E from its own old

@@ -23,13 +23,33 @@ ERAS = {"minkowski": AHS_MINKOWSKI, "radiation": AHS_RADIATION, "matter": AHS_MA
 PRECISIONS = {"fp32": _abi.AHS_PREC_FP32, "fp32c": _abi.AHS_PREC_FP32_COMPENSATED, "fp64": _abi.AHS_PREC_FP64}
 
 
+def stable_dt(dx: float, lambda0: float, e0: float, sigma: float, s: float, era: int, tau_end: float,
+              tau0: float = 1.0, s_cg: float = 0.0, tau_cg: float = 0.0, safety: float = 0.9) -> float:
+    """Largest leapfrog time step that stays stable up to conformal time tau_end,
+    times `safety`: dt omega_max < 2 with omega_max^2 = 12/dx^2 (the largest
+    eigenvalue of the lattice Laplacian and of the lattice curl-curl) plus the
+    larger of the Higgs and gauge masses squared, max(lambda0, 2 e0^2) sigma^2 c,
+    at the largest c = a^{2s} of the run (core-growth schedule included; c is
+    monotonic on each side of tau_cg).  Host arithmetic only."""
+    def c_of(eta):
+        a = (eta / tau0) ** era
+        if tau_cg > tau0 and eta >= tau_cg:
+            acg = (tau_cg / tau0) ** era
+            return acg ** (2 * s_cg) * (a / acg) ** (2 * s)
+        return a ** (2 * (s_cg if tau_cg > tau0 else s))
+    etas = [tau0, tau_end] + ([tau_cg] if tau0 < tau_cg < tau_end else [])
+    c_max = max(c_of(e) for e in etas)
+    w2 = 12.0 / dx ** 2 + max(lambda0, 2.0 * e0 ** 2) * sigma ** 2 * c_max
+    return safety * 2.0 / w2 ** 0.5
+
+
 class Lattice:
     """One N^3 lattice on the current CUDA device (owns its device memory)."""
 
     def __init__(self, N: int, dx: float = 0.5, dt: float = 0.1, lambda0: float = 2.0,
                  e0: float = 1.0, sigma: float = 1.0, s: float = 0.0, era=AHS_RADIATION,
                  measure_every: int = 10, stream: int | None = None, precision=None,
-                 momenta_in_place: bool = False):
+                 momenta_in_place: bool = False, core_growth=None):
         era = ERAS.get(era, era) if isinstance(era, str) else era
         self.N = N
         self.h = _abi.ahs_create(N, dx, dt, lambda0, e0, sigma, s, era)
@@ -39,6 +59,9 @@ class Lattice:
             _abi.ahs_set_option(self.h, _abi.AHS_OPT_PRECISION, precision)
         if momenta_in_place:
             _abi.ahs_set_option(self.h, _abi.AHS_OPT_MOMENTA_IN_PLACE, 1)
+        if core_growth is not None:          # (s_cg, tau_cg)
+            _abi.ahs_set_option(self.h, _abi.AHS_OPT_CORE_GROWTH_S, core_growth[0])
+            _abi.ahs_set_option(self.h, _abi.AHS_OPT_CORE_GROWTH_TAU, core_growth[1])
         if stream is not None:
             _abi.ahs_set_stream(self.h, stream)
 
@@ -159,6 +182,6 @@ class Batch:
         _abi.ahs_batch_autotune(self.b)
 
 
-__all__ = ["Lattice", "Batch", "AHSError", "ERAS", "PRECISIONS", "AHS_FIELD_ALL", "AHS_FIELD_E", "AHS_FIELD_LOW",
+__all__ = ["Lattice", "Batch", "stable_dt", "AHSError", "ERAS", "PRECISIONS", "AHS_FIELD_ALL", "AHS_FIELD_E", "AHS_FIELD_LOW",
            "AHS_FIELD_PHI", "AHS_FIELD_PI", "AHS_FIELD_THETA", "AHS_MATTER", "AHS_MINKOWSKI", "AHS_RADIATION",
            "AHS_PREC_FP32", "AHS_PREC_FP32_COMPENSATED", "AHS_PREC_FP64"]

@@ -402,6 +402,14 @@ int ahs_set_option(ahs_t *h, int key, double v)
         if (!(v >= 0) || !std::isfinite(v) || v >= 1.0) return fail(AHS_EINVAL, "cooling damping must be in [0, 1)");
         h->cooling = v;
         return ok();
+    case AHS_OPT_CORE_GROWTH_S:
+        if (!std::isfinite(v)) return fail(AHS_EINVAL, "core-growth s must be finite");
+        h->s_cg = v;
+        return ok();
+    case AHS_OPT_CORE_GROWTH_TAU:
+        if (!std::isfinite(v)) return fail(AHS_EINVAL, "core-growth end must be finite");
+        h->tau_cg = v;
+        return ok();
     case AHS_OPT_MOMENTA_IN_PLACE: {
         if (v != 0 && v != 1) return fail(AHS_EINVAL, "momenta_in_place must be 0 or 1");
         if ((int)v == h->inplace) return ok();
@@ -435,6 +443,8 @@ int ahs_get_option(ahs_t *h, int key, double *v)
     case AHS_OPT_PRECISION: *v = h->precision; break;
     case AHS_OPT_COOLING: *v = h->cooling; break;
     case AHS_OPT_MOMENTA_IN_PLACE: *v = h->inplace; break;
+    case AHS_OPT_CORE_GROWTH_S: *v = h->s_cg; break;
+    case AHS_OPT_CORE_GROWTH_TAU: *v = h->tau_cg; break;
     case AHS_OPT_TILE_Y: *v = step_shape(h->N, h->tile_y, h->zchunk).by; break;
     case AHS_OPT_ZCHUNK: *v = step_shape(h->N, h->tile_y, h->zchunk).dz; break;
     default: return fail(AHS_EINVAL, "unknown option %d", key);

@@ -570,6 +570,16 @@ int ahs_batch_set_option(ahs_batch_t *b, int key, double v)
         for (auto &p : b->prm) p.cooling = v;
         b->tables_dirty = true;
         return report_ok();
+    case AHS_OPT_CORE_GROWTH_S:
+        if (!std::isfinite(v)) return bfail(AHS_EINVAL, "core-growth s must be finite");
+        for (auto &p : b->prm) p.s_cg = v;
+        b->tables_dirty = true;
+        return report_ok();
+    case AHS_OPT_CORE_GROWTH_TAU:
+        if (!std::isfinite(v)) return bfail(AHS_EINVAL, "core-growth end must be finite");
+        for (auto &p : b->prm) p.tau_cg = v;
+        b->tables_dirty = true;
+        return report_ok();
     case AHS_OPT_TILE_Y:
         if (v != 8 && v != 16) return bfail(AHS_EINVAL, "tile_y must be 8 or 16");
         b->by = (int)v;
@@ -601,6 +611,8 @@ int ahs_batch_get_option(ahs_batch_t *b, int key, double *v)
     case AHS_OPT_WRAP_THETA: *v = b->prm[0].wrap; break;
     case AHS_OPT_PROFILE: *v = b->profile; break;
     case AHS_OPT_COOLING: *v = b->prm[0].cooling; break;
+    case AHS_OPT_CORE_GROWTH_S: *v = b->prm[0].s_cg; break;
+    case AHS_OPT_CORE_GROWTH_TAU: *v = b->prm[0].tau_cg; break;
     case AHS_OPT_TILE_Y: *v = b->by; break;
     case AHS_OPT_GRAPH: *v = b->use_graph; break;
     case AHS_OPT_STEP: *v = (double)b->n; break;

@@ -17,6 +17,8 @@ struct LatticeParams {
     double alpha = 2.0, tau0 = 1.0;
     int wrap = 0;
     double cooling = 0.0;   // > 0: cooling run, a = 1 and delta = omega = cooling
+    double s_cg = 0.0;      // core growth: s of the steps with eta < tau_cg
+    double tau_cg = 0.0;    // end of the core-growth period (<= tau0: none)
 };
 
 // FP64 scalars of step n (Eqs. 7, 8, 11, 12): eta, a, delta, omega, c = a^{2s}
@@ -30,8 +32,18 @@ inline Scalars scalars(const LatticeParams *h, int64_t n)
     r.eta = h->tau0 + (double)n * h->dt;
     r.a = std::pow(r.eta / h->tau0, (double)h->era);
     r.delta = 0.5 * h->alpha * (double)h->era * h->dt / r.eta;
-    r.omega = r.delta * (1.0 - h->s);
-    r.c = std::pow(r.a, 2.0 * h->s);
+    // core growth (Sec. 2, after Eq. 6): exponent s_cg before tau_cg and s after
+    // it, in omega and in c, with c continuous at tau_cg:
+    // c = a^{2 s_cg} before, a_cg^{2 s_cg} (a / a_cg)^{2 s} after
+    const bool grow = h->tau_cg > h->tau0;
+    const double s = grow && r.eta < h->tau_cg ? h->s_cg : h->s;
+    r.omega = r.delta * (1.0 - s);
+    if (grow && r.eta >= h->tau_cg) {
+        const double acg = std::pow(h->tau_cg / h->tau0, (double)h->era);
+        r.c = std::pow(acg, 2.0 * h->s_cg) * std::pow(r.a / acg, 2.0 * h->s);
+    } else {
+        r.c = std::pow(r.a, 2.0 * s);
+    }
     if (h->cooling > 0.0) {
         // cooling (the artificial damping period of Sec. 2): static background with
         // the same constant Crank-Nicolson damping on both momenta

@@ -119,3 +119,20 @@ def test_batch_bad_arguments(pkg):
         from paper_2005_14454_gb300 import _abi
         with pytest.raises(AHSError):
             _abi.ahs_batch_fields(b.b, 99, _abi.AHS_FIELD_ALL, 16)
+
+
+def test_batch_core_growth_equals_single_runs(pkg):
+    from paper_2005_14454_gb300._abi import AHS_OPT_CORE_GROWTH_S, AHS_OPT_CORE_GROWTH_TAU
+    members = [(16, 1, 21, 30), (20, 2, 22, 26)]
+    N, era, seed, end = zip(*members)
+    with pkg.Batch(N, era, seed, list(end), measure_every=5, s=1.0, **PARAMS) as b:
+        b.set_option(AHS_OPT_CORE_GROWTH_S, -1.0)
+        b.set_option(AHS_OPT_CORE_GROWTH_TAU, 2.05)
+        b.init()
+        b.run()
+        for i, (n, e, sd, ne) in enumerate(members):
+            with pkg.Lattice(n, era=e, s=1.0, measure_every=5, core_growth=(-1.0, 2.05), **PARAMS) as lat:
+                lat.init(sd)
+                lat.step(ne)
+                assert np.array_equal(b.state(i), lat.state()), i
+                assert b.records(i) == lat.records()

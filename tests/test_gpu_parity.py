@@ -333,6 +333,33 @@ def test_full_size_sampled_sites(eng, orc):
         assert np.allclose(A, r, rtol=2e-6, atol=2e-6), (A, r)
 
 
+# ------------------------------------------------------------------ core growth
+@pytest.mark.parametrize("era", [1, 2])
+def test_core_growth_matches_oracle(eng, orc, era):
+    """s = -1 until eta = 2.05, then s = 1 with c continuous (Sec. 2 core growth):
+    fields after the switch and every record of the run against the oracle."""
+    N = 24
+    with lattice(eng, N, era=era, s=1.0, measure_every=4, core_growth=(-1.0, 2.05)) as lat:
+        lat.init(31)
+        F0 = lat.state().astype(np.float64)
+        lat.step(18)
+        got = lat.state().astype(np.float64)
+        recs = lat.records()
+    p = oparams(orc, N, era=era, s=1.0, s_cg=-1.0, tau_cg=2.05)
+    ref = F0.copy()
+    n = 0
+    for r in recs:
+        orc.run(p, n, r["step"] - n, ref)
+        n = r["step"]
+        o = orc.measure(p, n, ref)
+        for k in ("e_total", "e_pot", "e_mag"):
+            assert r[k] == pytest.approx(o[k], rel=2e-5), (n, k)
+        assert r["gauss_max"] == pytest.approx(o["gauss_max"], rel=2e-2, abs=5e-6), n
+    orc.run(p, n, 18 - n, ref)
+    err = field_errors(got, ref)
+    assert max(err.values()) < 1e-5, err
+
+
 # ------------------------------------------------------------------ cooling, straight strings
 def test_cooled_vortex_pair_matches_oracle(eng, orc):
     """Straight vortex-antivortex pair along z relaxed by 200 cooling steps (a = 1,
