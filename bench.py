@@ -209,6 +209,18 @@ def cpu_baseline(seconds=12.0, N=128):
             "sample": f"FP64 oracle, {N}^3 lattice of the same workload, {steps} leapfrog steps in {dt:.1f} s"}
 
 
+def cpu_baseline_one_core(seconds=5.0, N=64):
+    """The same measurement on one core (a fresh interpreter with OMP_NUM_THREADS=1,
+    which the oracle's OpenMP runtime reads when it starts)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.cpu_baseline(%r, %d)))" % (ROOT, seconds, N))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        return {"error": out.stderr.strip().splitlines()[-1:] or ["failed"]}
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 # --------------------------------------------------------------------- ensemble
 ENSEMBLE = [(128, 24), (192, 16), (256, 8)]     # (side, realisations), half radiation / half matter
 
@@ -422,6 +434,7 @@ def run_ours(args, N):
         line["ensemble"] = run_ensemble(torch)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"]["one_core"] = cpu_baseline_one_core()
     group.close()
     print(json.dumps(line), flush=True)
     return 0

@@ -116,8 +116,9 @@ typedef struct ahs ahs_t;
  *   El = sum_i Ebar_i^2/(2 e0^2 c), B = sum_{i<j} (1 - cos alpha_ij)/(e0^2 c dx^4),
  *   L = K - G - V + El - B, rho = K + G + V + El + B, p = K - G/3 - V + (El+B)/3.
  * xi_l = sqrt(-mu Vol/(dx^3 sum L)) with mu = 2 pi sigma^2 (Eq. diagxi, left);
- * xi_w = sqrt(Vol/string_length), string_length = dx * n_wind, n_wind = sum |W_ij|
- * over all plaquettes (Eq. diagxi, right); v2_phi = 2R/(1+R), R = sum K L/sum G L
+ * xi_w = sqrt(Vol/string_length), string_length = (pi/6) dx n_wind, n_wind = sum
+ * |W_ij| over all plaquettes (Eq. diagxi, right; pi/6 corrects the Manhattan
+ * overcount of lattice paths, the convention of the paper's Table 1); v2_phi = 2R/(1+R), R = sum K L/sum G L
  * and v2_omega = (1 + 3 sum p L/sum rho L)/2 (Eq. diagvel, weight L).
  * gauss_*: residual of Gauss's law (Eq. 5 in discrete form) of the stored
  * momenta at n - 1/2 with phi^n.  nonfinite: number of sites whose diagnostic

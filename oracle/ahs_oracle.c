@@ -465,7 +465,11 @@ void orc_measure(const orc_params_t *p, int64_t n, const double *F, double *work
     o->v2_omega = 0.5 * (1.0 + 3.0 * t[QPL] / t[QRL]);
 
     o->n_wind = orc_windings(p, F, NULL);
-    o->string_length = dx * (double)o->n_wind;
+    /* string length from the pierced plaquettes with the pi/6 correction for the
+     * Manhattan overcount of lattice paths (reading G7: Eq. diagxi is silent on
+     * the length unit; the xi_dot_W of Table 1 is reproduced with this factor,
+     * not with the bare count) */
+    o->string_length = (M_PI / 6.0) * dx * (double)o->n_wind;
     o->xi_w = (o->n_wind > 0) ? sqrt(volume / o->string_length) : INFINITY;
 
     double g[2];

@@ -148,7 +148,9 @@ __device__ void reduce_rows(const double *__restrict__ part, int nb, const ObsSc
         o.v2_phi = 2.0 * R / (1.0 + R);
         o.v2_omega = 0.5 * (1.0 + 3.0 * S[Q_PL] / S[Q_RL]);
         o.n_wind = (int64_t)S[Q_WIND];
-        o.string_length = sc.dx * (double)o.n_wind;
+        // pierced plaquettes times dx, with the pi/6 correction for the Manhattan
+        // overcount of lattice paths (the convention Table 1's xi_dot_W follows)
+        o.string_length = (kPiD / 6.0) * sc.dx * (double)o.n_wind;
         o.xi_w = (o.n_wind > 0) ? sqrt(sc.volume / o.string_length) : INFINITY;
         o.gauss_rms = sqrt(S[Q_G2] / sc.sites);
         o.gauss_max = S[Q_GMAX];

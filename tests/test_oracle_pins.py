@@ -275,8 +275,8 @@ def test_vortex_pair_windings(orc, N):
     assert n2 == 2 * N
     o = orc.measure(p, 0, F)
     assert o["n_wind"] == 2 * N
-    assert o["string_length"] == pytest.approx(p.dx * 2 * N)
-    assert o["xi_w"] == pytest.approx(math.sqrt((N * p.dx) ** 3 / (p.dx * 2 * N)))
+    assert o["string_length"] == pytest.approx(math.pi / 6 * p.dx * 2 * N)
+    assert o["xi_w"] == pytest.approx(math.sqrt((N * p.dx) ** 3 / (math.pi / 6 * p.dx * 2 * N)))
 
 
 @pytest.mark.parametrize("N,R", [(8, 2), (12, 3)])
