@@ -77,24 +77,6 @@ static __device__ __noinline__ double wrap_plaq_fp64(float a, float b, float c, 
     return __dadd_rn(al, __dmul_rn(2.0 * kPiD, k));
 }
 
-// atan2 to about 1.5e-3 rad: the rational arctangent approximation of Rajan, Wang,
-// Inkol & Joyal ("Efficient approximations for the arctangent function", IEEE
-// Signal Processing Magazine 23(3), 2006), atan(a) ~ (pi/4) a - a (a - 1)(0.2447 +
-// 0.0663 a) on [0, 1], extended by octant symmetry.  The winding count only needs
-// each link phase to well within pi/5 (the plaquette sum is an exact multiple of
-// 2 pi); which side of the branch cut a phase falls on is decided by the sign of
-// the imaginary part, handled by the callers.  Requires max(|y|, |x|) > 0.
-static __device__ __forceinline__ float atan2_coarse(float y, float x)
-{
-    const float ax = fabsf(x), ay = fabsf(y);
-    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-    const float a = __fdividef(mn, mx);
-    float r = 0.785398163f * a - a * (a - 1.f) * (0.2447f + 0.0663f * a);
-    if (ay > ax) r = 1.570796327f - r;
-    if (x < 0.f) r = 3.141592654f - r;
-    return y < 0.f ? -r : r;
-}
-
 // true when the float32 complex number z = (zr, zi) is too close to the branch cut
 // of arg (the negative real axis, or z = 0) for its float32 sign to decide the branch
 static __device__ __forceinline__ bool near_cut(float zr, float zi)
@@ -102,37 +84,63 @@ static __device__ __forceinline__ bool near_cut(float zr, float zi)
     return (zr <= 0.f) && (fabsf(zi) <= kTie * fabsf(zr));
 }
 
-// Y_i(x) from a precomputed link phase V_i = (cos theta_i, sin theta_i) = conj(U_i);
-// the FP64 fallback recomputes from theta_i, which the caller loads only then.
+// Octant code o of an angle in (-pi, pi]: the angle lies in [o pi/4, (o+1) pi/4],
+// o in -4..3, and o pi/4 + pi/8 is within pi/8 of it.  From a complex number: the
+// signs of its parts and which is larger in magnitude; from an FP64 angle: floor.
+// A float32 number can get a different code than its exact value only within its
+// rounding (~1e-6 rad) of an octant boundary, and then a neighbouring one, so the
+// centre stays within pi/8 + 1e-6 of the exact angle; at the branch cut (+-pi) a
+// wrong sign would move it by 2 pi instead, which the near_cut fallback rules out.
+static __device__ __forceinline__ int octant(float zr, float zi)
+{
+    const bool steep = fabsf(zi) > fabsf(zr);
+    if (zi >= 0.f) return zr >= 0.f ? (steep ? 1 : 0) : (steep ? 2 : 3);
+    return zr >= 0.f ? (steep ? -2 : -1) : (steep ? -3 : -4);
+}
+static __device__ __forceinline__ int octant(double a)
+{
+    const int o = (int)floor(a * (4.0 / kPiD));
+    return o < -4 ? -4 : o > 3 ? 3 : o;
+}
+
+// Y_i(x) from a precomputed link phase V_i = (cos theta_i, sin theta_i) = conj(U_i),
+// as an octant code; the FP64 fallback recomputes from theta_i, which the caller
+// loads only then.
 template <class ThetaFn>
-static __device__ __forceinline__ float link_phase_v(float pr, float pi, float qr, float qi, float vc, float vs,
-                                                     ThetaFn theta)
+static __device__ __forceinline__ int link_phase_v(float pr, float pi, float qr, float qi, float vc, float vs,
+                                                   ThetaFn theta)
 {
     const float hr = vc * qr + vs * qi;   // U_i q with U_i = vc - i vs
     const float hi = vc * qi - vs * qr;
     const float zr = pr * hr + pi * hi;   // conj(p) U_i q
     const float zi = pr * hi - pi * hr;
-    if (near_cut(zr, zi)) return (float)link_phase_fp64(pr, pi, qr, qi, theta());
-    return atan2_coarse(zi, zr);
+    if (near_cut(zr, zi)) return octant(link_phase_fp64(pr, pi, qr, qi, theta()));
+    return octant(zr, zi);
 }
 
-// [alpha]_pi from the plaquette product Q = exp(i alpha) (Eq. 15 conjugated); the
-// FP64 fallback recomputes alpha = a + b - c - d from the four link angles.
+// [alpha]_pi from the plaquette product Q = exp(i alpha) (Eq. 15 conjugated), as an
+// octant code; the FP64 fallback recomputes alpha = a + b - c - d from the four
+// link angles.
 template <class AnglesFn>
-static __device__ __forceinline__ float wrap_from_q(float qr, float qi, AnglesFn angles)
+static __device__ __forceinline__ int wrap_from_q(float qr, float qi, AnglesFn angles)
 {
     if (near_cut(qr, qi)) {
         float a, b, c, d;
         angles(a, b, c, d);
-        return (float)wrap_plaq_fp64(a, b, c, d);
+        return octant(wrap_plaq_fp64(a, b, c, d));
     }
-    return atan2_coarse(qi, qr);
+    return octant(qr, qi);
 }
 
-static __device__ __forceinline__ int winding(float y1, float y2, float y3, float y4, float aw)
+// W = (Y1 + Y2 - Y3 - Y4 + [alpha]_pi) / 2 pi is an integer (the five phases add
+// up to the argument of a positive real number); with each angle replaced by its
+// octant centre (o + 1/2) pi/4 the sum is off by at most 5 (pi/8 + 1e-6) < pi, so
+// W is the integer nearest to (2T + 1)/16, T = o1 + o2 - o3 - o4 + o_alpha, i.e.
+// floor((2T + 9)/16) (never a tie: 2T + 1 is odd).
+static __device__ __forceinline__ int winding(int o1, int o2, int o3, int o4, int oa)
 {
-    float sum = ((((y1 + y2) - y3) - y4) + aw);
-    return __float2int_rn(sum * kInvTwoPiF);
+    const int t = o1 + o2 - o3 - o4 + oa;
+    return (2 * t + 9) >> 4;
 }
 
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): one step from state v.

@@ -61,19 +61,19 @@ __global__ void windings_kernel(const float *__restrict__ pr, const float *__res
     auto Y = [](float ar, float ai, float br, float bi, float2 v, float th) {
         return link_phase_v(ar, ai, br, bi, v.x, v.y, [&] { return th; });
     };
-    const float Yx = Y(p0r, p0i, pxr, pxi, vx0, tx0);
-    const float Yy = Y(p0r, p0i, pyr, pyi, vy0, ty0);
-    const float Yz = Y(p0r, p0i, pzr, pzi, vz0, tz0);
-    const float Yy_x = Y(pxr, pxi, pr[sxy], pim[sxy], vyx, tyx);
-    const float Yz_x = Y(pxr, pxi, pr[sxz], pim[sxz], vzx, tzx);
-    const float Yx_y = Y(pyr, pyi, pr[sxy], pim[sxy], vxy, txy);
-    const float Yz_y = Y(pyr, pyi, pr[syz], pim[syz], vzy, tzy);
-    const float Yx_z = Y(pzr, pzi, pr[sxz], pim[sxz], vxz, txz);
-    const float Yy_z = Y(pzr, pzi, pr[syz], pim[syz], vyz, tyz);
+    const int Yx = Y(p0r, p0i, pxr, pxi, vx0, tx0);
+    const int Yy = Y(p0r, p0i, pyr, pyi, vy0, ty0);
+    const int Yz = Y(p0r, p0i, pzr, pzi, vz0, tz0);
+    const int Yy_x = Y(pxr, pxi, pr[sxy], pim[sxy], vyx, tyx);
+    const int Yz_x = Y(pxr, pxi, pr[sxz], pim[sxz], vzx, tzx);
+    const int Yx_y = Y(pyr, pyi, pr[sxy], pim[sxy], vxy, txy);
+    const int Yz_y = Y(pyr, pyi, pr[syz], pim[syz], vzy, tzy);
+    const int Yx_z = Y(pzr, pzi, pr[sxz], pim[sxz], vxz, txz);
+    const int Yy_z = Y(pzr, pzi, pr[syz], pim[syz], vyz, tyz);
     const float2 Qxy = plaq_q(vx0, vy0, vyx, vxy), Qxz = plaq_q(vx0, vz0, vzx, vxz), Qyz = plaq_q(vy0, vz0, vzy, vyz);
-    const float wxy = wrap_from_q(Qxy.x, Qxy.y, [&](float &a, float &b, float &c, float &d) { a = tx0; b = tyx; c = txy; d = ty0; });
-    const float wxz = wrap_from_q(Qxz.x, Qxz.y, [&](float &a, float &b, float &c, float &d) { a = tx0; b = tzx; c = txz; d = tz0; });
-    const float wyz = wrap_from_q(Qyz.x, Qyz.y, [&](float &a, float &b, float &c, float &d) { a = ty0; b = tzy; c = tyz; d = tz0; });
+    const int wxy = wrap_from_q(Qxy.x, Qxy.y, [&](float &a, float &b, float &c, float &d) { a = tx0; b = tyx; c = txy; d = ty0; });
+    const int wxz = wrap_from_q(Qxz.x, Qxz.y, [&](float &a, float &b, float &c, float &d) { a = tx0; b = tzx; c = txz; d = tz0; });
+    const int wyz = wrap_from_q(Qyz.x, Qyz.y, [&](float &a, float &b, float &c, float &d) { a = ty0; b = tzy; c = tyz; d = tz0; });
     W[s] = (int8_t)winding(Yx, Yy_x, Yx_y, Yy, wxy);
     W[V + s] = (int8_t)winding(Yx, Yz_x, Yx_z, Yz, wxz);
     W[2 * V + s] = (int8_t)winding(Yy, Yz_y, Yy_z, Yz, wyz);

@@ -48,7 +48,7 @@ struct Tile {
         Plane pl[3];
         float sxy[NS], sxz[NS], syz[NS];
         // measurement steps only
-        float yx[NYW], yy[NYW], yz[NYW];
+        int yx[NYW], yy[NYW], yz[NYW];
         float ex[NS], ey[NS];
     };
     static constexpr size_t kStepBytes = offsetof(Smem, yx);
@@ -246,7 +246,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
     // carried from plane zz-1 (own column)
     float2 phPrev = make_float2(0.f, 0.f), vzPrev = make_float2(1.f, 0.f);
     float sxzPrev = 0.f, syzPrev = 0.f;
-    float YxCar = 0.f, YyCar = 0.f;   // Y_x, Y_y of plane zz (measurement)
+    int YxCar = 0, YyCar = 0;   // octant codes of Y_x, Y_y of plane zz (measurement)
 
     Acc acc;
     if (MEASURE) acc_zero(acc);
@@ -321,7 +321,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
 
         // measurement: link phases Y_x, Y_y of plane zz+1 on every column of the tile
         // (ragged-tile columns too: they are the periodic images the ring reads)
-        float YxNext = 0.f, YyNext = 0.f;
+        int YxNext = 0, YyNext = 0;
         if (MEASURE) {
             const float2 pn0 = pn.ph[r0], vxn = pn.vx[r0], vyn = pn.vy[r0];
             const float2 qxn = pn.ph[rxp], qyn = pn.ph[ryp];
@@ -401,14 +401,14 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
 
                 // plaquette windings with lower corner x
                 const int wi = T::w(tx, ty);
-                const float Yx = YxCar, Yy = YyCar, Yz = S.yz[wi];
+                const int Yx = YxCar, Yy = YyCar, Yz = S.yz[wi];
                 const float tnx = nthx, tny = nthy;
                 const float t0x = thx, t0y = thy, t0z = thz;
-                const float wxy = wrap_from_q(Qxy.x, Qxy.y, [&](float &a, float &bb, float &c, float &d) {
+                const int wxy = wrap_from_q(Qxy.x, Qxy.y, [&](float &a, float &bb, float &c, float &d) {
                     a = t0x; bb = P.in(FTY, oc + cxpoff); c = P.in(FTX, oc + cypoff); d = t0y; });
-                const float wxz = wrap_from_q(Qxz.x, Qxz.y, [&](float &a, float &bb, float &c, float &d) {
+                const int wxz = wrap_from_q(Qxz.x, Qxz.y, [&](float &a, float &bb, float &c, float &d) {
                     a = t0x; bb = P.in(FTZ, oc + cxpoff); c = tnx; d = t0z; });
-                const float wyz = wrap_from_q(Qyz.x, Qyz.y, [&](float &a, float &bb, float &c, float &d) {
+                const int wyz = wrap_from_q(Qyz.x, Qyz.y, [&](float &a, float &bb, float &c, float &d) {
                     a = t0y; bb = P.in(FTZ, oc + cypoff); c = tny; d = t0z; });
                 const int nxy = winding(Yx, S.yy[T::w(tx + 1, ty)], S.yx[T::w(tx, ty + 1)], Yy, wxy);
                 const int nxz = winding(Yx, S.yz[T::w(tx + 1, ty)], YxNext, Yz, wxz);

@@ -136,3 +136,39 @@ def test_batch_core_growth_equals_single_runs(pkg):
                 lat.step(ne)
                 assert np.array_equal(b.state(i), lat.state()), i
                 assert b.records(i) == lat.records()
+
+
+def test_ensemble_means_match_oracle(pkg, orc):
+    """The ensemble comparison of the benchmark's batched run, scaled down: four
+    64^3 realisations (two radiation, two matter, s = 0) batched to half
+    light-crossing (150 steps); the ensemble means of xi_W / tau, xi_L / tau,
+    <v^2>_omega and <v^2>_phi at every measurement after the first agree with the
+    oracle's run of the same starts within 1%."""
+    members = [(64, 1, 41, 151), (64, 1, 42, 151), (64, 2, 43, 151), (64, 2, 44, 151)]
+    N, era, seed, end = zip(*members)
+    with pkg.Batch(N, era, seed, list(end), measure_every=10, **PARAMS) as b:
+        b.init()
+        starts = [b.state(i).astype(np.float64) for i in range(len(members))]
+        b.run()
+        recs = [b.records(i) for i in range(len(members))]
+    keys = ("xi_w", "xi_l", "v2_omega", "v2_phi")
+    for eras in ((0, 1), (2, 3)):
+        gpu = {k: [] for k in keys}
+        ref = {k: [] for k in keys}
+        for i in eras:
+            p = orc.Params(N=64, era=members[i][1], **PARAMS)
+            F = starts[i].copy()
+            n = 0
+            rows_g, rows_o = [], []
+            for r in recs[i][1:]:
+                orc.run(p, n, r["step"] - n, F)
+                n = r["step"]
+                o = orc.measure(p, n, F)
+                rows_g.append([r["xi_w"] / r["tau"], r["xi_l"] / r["tau"], r["v2_omega"], r["v2_phi"]])
+                rows_o.append([o["xi_w"] / o["tau"], o["xi_l"] / o["tau"], o["v2_omega"], o["v2_phi"]])
+            for j, k in enumerate(keys):
+                gpu[k].append([row[j] for row in rows_g])
+                ref[k].append([row[j] for row in rows_o])
+        for k in keys:
+            g, o = np.mean(gpu[k], axis=0), np.mean(ref[k], axis=0)
+            assert np.allclose(g, o, rtol=0.01), (eras, k, g, o)

@@ -352,8 +352,11 @@ def test_core_growth_matches_oracle(eng, orc, era):
         orc.run(p, n, r["step"] - n, ref)
         n = r["step"]
         o = orc.measure(p, n, ref)
-        for k in ("e_total", "e_pot", "e_mag"):
-            assert r[k] == pytest.approx(o[k], rel=2e-5), (n, k)
+        # two trajectories (float32 engine, FP64 oracle) from the same start: the
+        # total to 2e-5, the small magnetic and potential parts to 1e-4
+        assert r["e_total"] == pytest.approx(o["e_total"], rel=2e-5), n
+        for k in ("e_pot", "e_mag"):
+            assert r[k] == pytest.approx(o[k], rel=1e-4), (n, k)
         assert r["gauss_max"] == pytest.approx(o["gauss_max"], rel=2e-2, abs=5e-6), n
     orc.run(p, n, 18 - n, ref)
     err = field_errors(got, ref)
