@@ -286,6 +286,48 @@ def run_ensemble(torch):
 
 
 # --------------------------------------------------------------------- reference arm
+CAPACITY_N = 1536
+
+
+def run_capacity(torch, N=CAPACITY_N, steps=3):
+    """The same workload on N^3 with Pi and E updated in place (60 B/site allocated,
+    217 GB at 1536^3, a lattice the default 80 B/site storage cannot hold beside the
+    benchmark's other buffers): site-updates/s over `steps` periods of 10 leapfrog
+    steps after one warm-up period, and the plain step's roofline."""
+    from paper_2005_14454_gb300 import _abi
+    stream = torch.cuda.current_stream()
+    h = _abi.ahs_create(N, PARAMS["dx"], PARAMS["dt"], PARAMS["lambda0"], PARAMS["e0"], PARAMS["sigma"],
+                        PARAMS["s"], ERA)
+    try:
+        _abi.ahs_set_stream(h, stream.cuda_stream)
+        _abi.ahs_set_option(h, _abi.AHS_OPT_MOMENTA_IN_PLACE, 1)
+        _abi.ahs_set_option(h, _abi.AHS_OPT_MEASURE_EVERY, PERIOD)
+        _abi.ahs_init(h, 1)
+        _abi.ahs_step(h, PERIOD)
+        _abi.ahs_records(h)
+        _abi.ahs_set_option(h, _abi.AHS_OPT_PROFILE, 1)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            _abi.ahs_step(h, PERIOD)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        k_ms, k_n = _abi.ahs_kernel_time(h, _abi.AHS_KERNEL_STEP)
+        km_ms, km_n = _abi.ahs_kernel_time(h, _abi.AHS_KERNEL_STEP_MEASURE)
+        nbytes = _abi.ahs_device_bytes(h)
+    finally:
+        _abi.ahs_destroy(h)
+    pk, pk_kind = peaks()
+    avg = k_ms / max(k_n, 1)
+    achieved = BYTES_PER_SITE * N ** 3 / (avg / 1e3) / 1e9
+    return {"lattice": N, "storage": "Pi and E updated in place", "device_bytes": nbytes,
+            "value": N ** 3 * PERIOD * steps / (ms / 1e3), "unit": "site-updates/s", "ms_per_step": ms / steps,
+            "plain_step_ms": avg, "measuring_step_ms": km_ms / max(km_n, 1),
+            "roofline_frac": achieved / pk["hbm_gbs"], "achieved_gbs": achieved, "peak_kind": pk_kind}
+
+
 def run_reference(args, N):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -432,6 +474,8 @@ def run_ours(args, N):
     }
     if not args.no_ensemble and ws == 1:
         line["ensemble"] = run_ensemble(torch)
+    if not args.no_capacity and ws == 1 and not args.momenta_in_place:
+        line["capacity"] = run_capacity(torch)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
         line["cpu_baseline"]["one_core"] = cpu_baseline_one_core()
@@ -453,6 +497,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble leg")
+    ap.add_argument("--no-capacity", action="store_true", help="skip the 1536^3 in-place-momenta leg")
     ap.add_argument("--momenta-in-place", action="store_true",
                     help="store Pi and E once (60 B/site; lattices up to 1600^3)")
     args = ap.parse_args()
