@@ -461,8 +461,11 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
     if (MEASURE) block_reduce_store<32 * BY>(acc, partial_row);
 }
 
+// Residency: a plain step fits 64 registers, so four 8-warp CTAs share an SM
+// (32 warps); the measuring step needs 128 (two CTAs).
 template <int BY, bool MEASURE, bool STORE, bool COMP>
-__global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, int N, int Dz, double *partials)
+__global__ void __launch_bounds__(32 * BY, (MEASURE ? 16 : 32) / BY)
+    step_tiled(StepPtrs P, StepCoef k, int N, int Dz, double *partials)
 {
     using T = Tile<BY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -479,7 +482,7 @@ __global__ void __launch_bounds__(32 * BY) step_tiled(StepPtrs P, StepCoef k, in
 // tiles of members still running form the prefix live[n].  The member's field
 // base and coefficients are staged per tile.
 template <int BY, bool MEASURE>
-__global__ void __launch_bounds__(32 * BY, (MEASURE ? 16 : 24) / BY) batch_step(BatchLaunch L, int dn)
+__global__ void __launch_bounds__(32 * BY, (MEASURE ? 16 : 32) / BY) batch_step(BatchLaunch L, int dn)
 {
     using T = Tile<BY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
