@@ -15,9 +15,8 @@
  * theta_i = dx * A_i is the compact link angle; the link variable is
  * U_i(x) = exp(-i theta_i(x))  (Eq. 13, with the dx of Eq. 16).
  *
- * Readings of passages the paper leaves silent or garbled are listed in the
- * design notes of the repository; the ones that change arithmetic are repeated
- * beside the code they affect.
+ * Where the paper is silent or garbled, the reading taken is stated beside the
+ * code it affects.
  *
  * Each function is a literal transcription of one definition: no blocking, no
  * fusion, loops in site order.  OpenMP only splits independent site loops;
@@ -466,7 +465,7 @@ void orc_measure(const orc_params_t *p, int64_t n, const double *F, double *work
 
     o->n_wind = orc_windings(p, F, NULL);
     /* string length from the pierced plaquettes with the pi/6 correction for the
-     * Manhattan overcount of lattice paths (reading G7: Eq. diagxi is silent on
+     * Manhattan overcount of lattice paths (Eq. diagxi is silent on
      * the length unit; the xi_dot_W of Table 1 is reproduced with this factor,
      * not with the bare count) */
     o->string_length = (M_PI / 6.0) * dx * (double)o->n_wind;

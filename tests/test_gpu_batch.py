@@ -172,3 +172,36 @@ def test_ensemble_means_match_oracle(pkg, orc):
         for k in keys:
             g, o = np.mean(gpu[k], axis=0), np.mean(ref[k], axis=0)
             assert np.allclose(g, o, rtol=0.01), (eras, k, g, o)
+
+
+def test_benchmark_ensemble_128_members_match_oracle(pkg, orc):
+    """The first four 128^3 realisations of the benchmark's ensemble (seeds 1-4,
+    radiation and matter alternating, s = 0, 310 steps to half light-crossing,
+    measurement every 10 steps) run as one batch: ensemble means of xi_W / tau and
+    of both velocity estimators at every measurement after the first within 1% of
+    the oracle's runs from the same starts."""
+    members = [(128, 1, 1, 311), (128, 2, 2, 311), (128, 1, 3, 311), (128, 2, 4, 311)]
+    N, era, seed, end = zip(*members)
+    with pkg.Batch(N, era, seed, list(end), measure_every=10, **PARAMS) as b:
+        b.init()
+        starts = [b.state(i).astype(np.float64) for i in range(len(members))]
+        b.run()
+        recs = [b.records(i) for i in range(len(members))]
+    keys = ("xi_w", "v2_omega", "v2_phi")
+    gpu, ref = [], []
+    for i, (n, e, sd, ne) in enumerate(members):
+        p = orc.Params(N=n, era=e, **PARAMS)
+        F = starts[i]
+        k = 0
+        rg, ro = [], []
+        for r in recs[i][1:]:
+            orc.run(p, k, r["step"] - k, F)
+            k = r["step"]
+            o = orc.measure(p, k, F)
+            rg.append([r["xi_w"] / r["tau"], r["v2_omega"], r["v2_phi"]])
+            ro.append([o["xi_w"] / o["tau"], o["v2_omega"], o["v2_phi"]])
+        gpu.append(rg)
+        ref.append(ro)
+    g, o = np.mean(gpu, axis=0), np.mean(ref, axis=0)
+    for j, k in enumerate(keys):
+        assert np.allclose(g[:, j], o[:, j], rtol=0.01), (k, g[:, j], o[:, j])

@@ -4,8 +4,8 @@
   every 10 steps: every record's xi_W, xi_L, <v^2>_phi and <v^2>_omega within 1% of
   the oracle's, winding counts close (the float32 and FP64 trajectories separate
   only slowly over 150 steps of this damped run).
-* matter era with s = 1 (BASELINE's second configuration) is beyond the leapfrog
-  stability bound from eta ~ 3.6 on (reading G13 of the design notes): engine and
+* matter era with s = 1 (the 256^3 benchmark configuration) is beyond the leapfrog
+  stability bound dt^2 omega_max^2 < 4 from eta ~ 3.6 on: engine and
   oracle agree step by step until the energy blows up, and the blow-up happens at
   the same step.
 """
@@ -87,7 +87,7 @@ def test_matter_s1_instability_onset_matches_oracle(pkg, orc):
 
 
 def test_matter_s1_256_runs_to_the_monitor(pkg):
-    """BASELINE's 256^3 matter, s = 1 configuration on the GPU: the fused measurement
+    """The 256^3 matter-era, s = 1 configuration on the GPU: the fused measurement
     reports non-finite sites (the step call returns AHS_ENONFINITE) well before
     tau = 64; the step it trips at is reported."""
     from paper_2005_14454_gb300 import AHSError

@@ -419,8 +419,8 @@ def test_measure_closed_form_twisted_state(orc):
 
 # --------------------------------------------------------------------------- cooling
 def test_cooling_relaxes_vortex_pair_and_keeps_windings(orc):
-    # cooling: a = 1, delta = omega = 0.5 (the damping period of Sec. 2, reading
-    # of the design notes).  Dissipative: the energy falls; topological: the two
+    # cooling: a = 1, delta = omega = 0.5 (the damping period Sec. 2 mentions, read
+    # as a static background with constant damping).  Dissipative: the energy falls; topological: the two
     # hand-placed straight strings keep winding +-1 on every z-layer; Gauss's law
     # stays exact (delta = omega, c = 1).  At critical coupling (beta = lambda0 /
     # 2 e0^2 = 1) the relaxed straight string is the BPS vortex, whose energy per
@@ -521,7 +521,7 @@ def test_core_growth_keeps_strings_resolved(orc):
 
 
 def test_stable_time_step_bound(orc):
-    """Leapfrog stability (reading G13): dt * omega_max < 2 with omega_max^2 =
+    """Leapfrog stability: dt * omega_max < 2 with omega_max^2 =
     12/dx^2 + max(lambda0, 2 e0^2) sigma^2 c_max.  The matter era with s = 1 at
     dt = 0.1 breaks the bound near eta = 3.6 and the oracle's energy blows up
     before eta = 5; at the step the bound gives for eta_end = 5 the same start
