@@ -76,7 +76,7 @@ static inline int64_t nb(int N, int x, int y, int z, int i, int d)
 }
 
 /* ---------------------------------------------------------------------------
- * O1  time-dependent scalars (Eqs. 7, 8, 11, 12).
+ * time-dependent scalars (Eqs. 7, 8, 11, 12).
  *   eta_n = eta0 + n dt,  a_n = (eta_n/eta0)^p,
  *   delta_n = (alpha/2) p dt/eta_n   (d ln a / d ln eta = p),
  *   omega_n = delta_n (1 - s),  c_n = a_n^{2s}.
@@ -132,7 +132,7 @@ double orc_uniform(uint64_t seed, uint64_t idx)
     return (double)(sm64(seed ^ sm64(idx)) >> 11) * (1.0 / 9007199254740992.0);
 }
 
-/* O9  random-phase initial condition (Sec. 2): phi = sigma e^{i vartheta},
+/* random-phase initial condition (Sec. 2): phi = sigma e^{i vartheta},
  * every other field zero. */
 void orc_init(const orc_params_t *p, uint64_t seed, double *F)
 {
@@ -231,7 +231,7 @@ void orc_forces(const orc_params_t *p, int64_t n, const double *F, double *out)
 }
 
 /* ---------------------------------------------------------------------------
- * O3/O4  kick of step n (Eqs. 7, 8): Crank-Nicolson damping, leapfrog force.
+ * kick of step n (Eqs. 7, 8): Crank-Nicolson damping, leapfrog force.
  *   (1+delta) Pi^{n+1/2}  = (1-delta) Pi^{n-1/2}  + dt FPi
  *   (1+omega) E_i^{n+1/2} = (1-omega) E_i^{n-1/2} + dt FE_i
  * Writes the new momenta into out (5 planes: Re Pi, Im Pi, E_x, E_y, E_z);
@@ -253,7 +253,7 @@ void orc_kick(const orc_params_t *p, int64_t n, const double *F, double *out)
     }
 }
 
-/* O5  drift (Eqs. 9, 10): phi += dt Pi^{n+1/2}, theta_i += dt dx E_i^{n+1/2}. */
+/* drift (Eqs. 9, 10): phi += dt Pi^{n+1/2}, theta_i += dt dx E_i^{n+1/2}. */
 void orc_drift(const orc_params_t *p, double *F)
 {
     const int64_t V = vol(p->N);
@@ -296,7 +296,7 @@ double orc_wrap(double a)
 }
 
 /* ---------------------------------------------------------------------------
- * O7  plaquette windings (gauge-invariant lattice winding of Kajantie et al.
+ * plaquette windings (gauge-invariant lattice winding of Kajantie et al.
  * 1998, cited by the paper for xi_W).  With
  *   Y_i(x) = arg( phi*(x) U_i(x) phi(x+i) )  in (-pi, pi]
  *   W_ij(x) = ( Y_i(x) + Y_j(x+i) - Y_i(x+j) - Y_j(x) + [alpha_ij(x)]_pi ) / 2pi
@@ -343,7 +343,7 @@ int64_t orc_windings(const orc_params_t *p, const double *F, int8_t *W)
 }
 
 /* ---------------------------------------------------------------------------
- * O8  Gauss-law residual of the momenta stored in F (time n-1/2), evaluated
+ * Gauss-law residual of the momenta stored in F (time n-1/2), evaluated
  * with phi^n:
  *   G(x) = sum_i (E_i(x) - E_i(x-i))/dx - 2 e0^2 kappa Im[phi*(x) Pi(x)]
  * where kappa = c_{n-1} (1+delta_{n-1})/(1+omega_{n-1}) is the factor the
@@ -381,7 +381,7 @@ void orc_gauss(const orc_params_t *p, int64_t n, const double *F, double *G, dou
 }
 
 /* ---------------------------------------------------------------------------
- * O6  measurement at integer time n, from phi^n, theta^n and the momenta
+ * measurement at integer time n, from phi^n, theta^n and the momenta
  * averaged over the kick of step n:  Pibar = (Pi^{n-1/2} + Pi^{n+1/2})/2,
  * Ebar likewise.  Per site (Lagrangian of Eq. 1 on the lattice, with the
  * coupling scalings of Eqs. 7, 8 absorbed in c_n = a^{2s}):
@@ -477,7 +477,7 @@ void orc_measure(const orc_params_t *p, int64_t n, const double *F, double *work
 }
 
 /* ---------------------------------------------------------------------------
- * Lattice Hamiltonian at time n (the energy of O6 with the stored momenta
+ * Lattice Hamiltonian at time n (the energy of the measurement with the stored momenta
  * taken as they are, no averaging):
  *   H = dx^3 sum_x [ |Pi|^2 + G + V + El + B ]
  * Used by the force and energy-conservation pins.

@@ -76,7 +76,7 @@ def test_scalars_eras(orc):
     assert sc["a"] == 1.0 and sc["delta"] == 0.0 and sc["omega"] == 0.0 and sc["c"] == 1.0
 
 
-# --------------------------------------------------------------------------- T7 vacuum
+# --------------------------------------------------------------------------- vacuum
 @pytest.mark.parametrize("era,s", [(0, 0.0), (1, 0.0), (2, 0.0), (2, 1.0)])
 def test_vacuum_fixed_point(orc, era, s):
     p = P(orc, 6, era=era, s=s)
@@ -102,7 +102,7 @@ def test_init_random_phase(orc):
     assert abs(np.mean(np.cos(ang))) < 0.15 and abs(np.mean(np.sin(ang))) < 0.15
 
 
-# --------------------------------------------------------------------------- T1 Gauss
+# --------------------------------------------------------------------------- Gauss
 @pytest.mark.parametrize("era,s", [(0, 0.0), (1, 0.0), (2, 0.0), (1, 1.0), (0, 1.0)])
 def test_gauss_law_preserved(orc, era, s):
     p = P(orc, 8, era=era, s=s)
@@ -126,7 +126,7 @@ def test_gauss_law_detects_broken_damping(orc):
     assert mx > 1e-6
 
 
-# --------------------------------------------------------------------------- T2 energy
+# --------------------------------------------------------------------------- energy
 def _energy_series(orc, dt, steps, seed=3):
     p = P(orc, 8, era=0, dt=dt)
     F = inputs.smooth_state(8, seed, amp=0.1)
@@ -148,7 +148,7 @@ def test_minkowski_energy_second_order(orc):
     assert 3.7 < d1 / d2 < 4.3, (d1, d2)
 
 
-# --------------------------------------------------------------------------- T3 forces
+# --------------------------------------------------------------------------- forces
 @pytest.mark.parametrize("era,s,n", [(0, 0.0, 0), (2, 1.0, 3), (1, 0.5, 5)])
 def test_forces_are_minus_grad_H(orc, era, s, n):
     N = 4
@@ -175,7 +175,7 @@ def test_forces_are_minus_grad_H(orc, era, s, n):
             assert got == pytest.approx(want, rel=2e-7, abs=2e-7 * (1 + abs(want)))
 
 
-# --------------------------------------------------------------------------- T4 gauge
+# --------------------------------------------------------------------------- gauge
 def _gauge(F, chi):
     G = F.copy()
     e = np.exp(1j * chi)
@@ -213,7 +213,7 @@ def test_gauge_invariance(orc):
     assert np.abs(d).max() < 1e-11
 
 
-# --------------------------------------------------------------------------- T5 reversal
+# --------------------------------------------------------------------------- reversal
 def test_time_reversal_minkowski(orc):
     N = 6
     p = P(orc, N, era=0)
@@ -229,7 +229,7 @@ def test_time_reversal_minkowski(orc):
     assert np.abs(F - F0).max() < 1e-11
 
 
-# --------------------------------------------------------------------------- T6 dispersion
+# --------------------------------------------------------------------------- dispersion
 @pytest.mark.parametrize("mode", ["higgs", "photon"])
 def test_linear_dispersion(orc, mode):
     N = 8
@@ -257,7 +257,7 @@ def test_linear_dispersion(orc, mode):
     assert np.allclose(lhs, rhs, rtol=0, atol=1e-6 * eps)
 
 
-# --------------------------------------------------------------------------- T8 windings
+# --------------------------------------------------------------------------- windings
 @pytest.mark.parametrize("N", [8, 12])
 def test_vortex_pair_windings(orc, N):
     p = P(orc, N)
@@ -318,7 +318,7 @@ def test_wrap(orc):
     assert orc.wrap(2 * math.pi + 0.25) == pytest.approx(0.25)
 
 
-# --------------------------------------------------------------------------- T9 symmetries
+# --------------------------------------------------------------------------- symmetries
 def test_translation_commutes_bitwise(orc):
     N = 6
     p = P(orc, N, era=1)
@@ -358,7 +358,7 @@ def test_global_phase_commutes(orc):
     assert np.abs(_gauge(F, np.full((N, N, N), 0.7)) - G).max() < 1e-12
 
 
-# --------------------------------------------------------------------------- O6 checks
+# --------------------------------------------------------------------------- measurement
 def test_measure_closed_form_uniform_state(orc):
     # uniform phi of modulus r, uniform Pi and E, zero links: every site identical,
     # G = B = 0, the kick changes only Pi (potential) and leaves E alone.
