@@ -182,3 +182,58 @@ def test_precision_study_small_lattice_against_oracle(pkg, orc):
         else:
             assert recs[-1]["gauss_rms"] < 1e-4
     print("energy drift", drift)
+
+
+OBSERVABLES = ("e_total", "e_kin", "e_grad", "e_pot", "e_elec", "e_mag", "lagrangian", "xi_l", "xi_w",
+               "v2_phi", "v2_omega", "gauss_rms")
+
+
+def test_error_per_observable_against_oracle(pkg, orc):
+    """The error of every observable against the FP64 oracle, per precision mode, on
+    the 64^3 radiation workload (s = 0, 150 steps to tau = 16, a record every 10
+    steps) from one float32 start: (a) along the run (engine and oracle each
+    evolve; the difference includes the trajectories' divergence) and (b) of the
+    measurement alone, on the engine's final snapshot.  Printed as one JSON line
+    (`pytest -s`) and bounded here."""
+    import json
+    N, steps, every = 64, 150, 10
+    p = orc.Params(N=N, era=1, **PARAMS)
+    with pkg.Lattice(N, era=1, measure_every=0, **PARAMS) as lat:
+        lat.init(2024)
+        F0 = lat.state().astype(np.float64)
+    ref, F = {}, F0.copy()
+    for n in range(0, steps + 1, every):
+        ref[n] = orc.measure(p, n, F)
+        if n < steps:
+            orc.run(p, n, every, F)
+    table = {}
+    for mode in ("fp32", "fp32c", "fp64"):
+        with pkg.Lattice(N, era=1, measure_every=every, precision=mode, **PARAMS) as lat:
+            lat.set_state(F0)
+            lat.step(steps)
+            recs = {r["step"]: r for r in lat.records()}
+            recs[steps] = lat.measure()
+            snap = lat.state().astype(np.float64)
+            if mode == "fp32c":
+                from paper_2005_14454_gb300 import AHS_FIELD_LOW
+                lo = lat.field(AHS_FIELD_LOW).astype(np.float64)
+                snap[2:4] += lo[0:2]
+                snap[7:10] += lo[2:5]
+        same = orc.measure(p, steps, snap)
+        row = {}
+        for k in OBSERVABLES:
+            run_err = max(abs(recs[n][k] - ref[n][k]) / abs(ref[n][k]) for n in ref if n > 0)
+            meas_err = abs(recs[steps][k] - same[k]) / abs(same[k])
+            row[k] = [run_err, meas_err]
+        row["n_wind"] = [max(abs(recs[n]["n_wind"] - ref[n]["n_wind"]) for n in ref),
+                         abs(recs[steps]["n_wind"] - same["n_wind"])]
+        table[mode] = row
+    print(json.dumps({"observable_errors": table}))
+    for mode, row in table.items():
+        assert row["n_wind"][1] == 0                     # windings exact on the same snapshot
+        for k in OBSERVABLES:
+            run_err, meas_err = row[k]
+            if k == "gauss_rms":
+                continue                                 # a residual: rounding level, not relative
+            assert meas_err < (1e-10 if mode == "fp64" else 2e-4), (mode, k, meas_err)
+            assert run_err < (1e-8 if mode == "fp64" else 1e-2), (mode, k, run_err)
