@@ -137,7 +137,7 @@ StepPtrs64 pointers64(const ahs_t *h)
 // CTAs (rows of partials) of the current step launch
 int launch_blocks(const ahs_t *h)
 {
-    if (h->precision == AHS_PREC_FP64) return step_shape_fp64(h->N).blocks;
+    if (h->precision == AHS_PREC_FP64) return step_shape(h->N, 8, h->zchunk).blocks;
     return step_shape(h->N, h->tile_y, h->zchunk).blocks;
 }
 
@@ -145,7 +145,8 @@ int launch_blocks(const ahs_t *h)
 cudaError_t launch_current(const ahs_t *h, bool measure, bool store)
 {
     if (h->precision == AHS_PREC_FP64)
-        return launch_step_fp64(pointers64(h), coefficients64(h, h->n), h->N, measure, store, h->partials, h->stream);
+        return launch_step64(pointers64(h), coefficients64(h, h->n), h->N, step_shape(h->N, 8, h->zchunk), measure,
+                             store, h->partials, h->stream);
     return launch_step(pointers(h), coefficients(h, h->n), h->N, step_shape(h->N, h->tile_y, h->zchunk), measure, store,
                        h->partials, h->stream, h->precision == AHS_PREC_FP32_COMPENSATED);
 }
@@ -445,7 +446,7 @@ int ahs_get_option(ahs_t *h, int key, double *v)
     case AHS_OPT_MOMENTA_IN_PLACE: *v = h->inplace; break;
     case AHS_OPT_CORE_GROWTH_S: *v = h->s_cg; break;
     case AHS_OPT_CORE_GROWTH_TAU: *v = h->tau_cg; break;
-    case AHS_OPT_TILE_Y: *v = step_shape(h->N, h->tile_y, h->zchunk).by; break;
+    case AHS_OPT_TILE_Y: *v = h->precision == AHS_PREC_FP64 ? 8 : step_shape(h->N, h->tile_y, h->zchunk).by; break;
     case AHS_OPT_ZCHUNK: *v = step_shape(h->N, h->tile_y, h->zchunk).dz; break;
     default: return fail(AHS_EINVAL, "unknown option %d", key);
     }

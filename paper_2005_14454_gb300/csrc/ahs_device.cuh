@@ -56,7 +56,8 @@ static __device__ __forceinline__ void link_sincos(float th, float &s, float &c)
 
 // ---------------------------------------------------------------- windings
 // Y_i(x) = arg(phi^*(x) U_i(x) phi(x+i)), U_i = exp(-i theta_i).
-static __device__ __noinline__ double link_phase_fp64(float pr, float pi, float qr, float qi, float th)
+template <class In>
+static __device__ __noinline__ double link_phase_fp64(In pr, In pi, In qr, In qi, In th)
 {
     double s, c;
     sincos((double)th, &s, &c);
@@ -70,18 +71,21 @@ static __device__ __noinline__ double link_phase_fp64(float pr, float pi, float 
 
 // [alpha]_pi of alpha = a + b - c - d: wrapped into (-pi, pi] by
 // alpha + 2 pi floor((pi - alpha)/(2 pi)).
-static __device__ __noinline__ double wrap_plaq_fp64(float a, float b, float c, float d)
+template <class In>
+static __device__ __noinline__ double wrap_plaq_fp64(In a, In b, In c, In d)
 {
     double al = __dsub_rn(__dsub_rn(__dadd_rn((double)a, (double)b), (double)c), (double)d);
     double k = floor(__ddiv_rn(__dsub_rn(kPiD, al), 2.0 * kPiD));
     return __dadd_rn(al, __dmul_rn(2.0 * kPiD, k));
 }
 
-// true when the float32 complex number z = (zr, zi) is too close to the branch cut
-// of arg (the negative real axis, or z = 0) for its float32 sign to decide the branch
-static __device__ __forceinline__ bool near_cut(float zr, float zi)
+// true when the complex number z = (zr, zi) is too close to the branch cut of arg
+// (the negative real axis, or z = 0) for the sign of its computed imaginary part to
+// decide the branch (float32; FP64 fields use the same margin)
+template <class R>
+static __device__ __forceinline__ bool near_cut(R zr, R zi)
 {
-    return (zr <= 0.f) && (fabsf(zi) <= kTie * fabsf(zr));
+    return (zr <= R(0)) && (fabs(zi) <= R(kTie) * fabs(zr));
 }
 
 // Octant code o of an angle in (-pi, pi]: the angle lies in [o pi/4, (o+1) pi/4],
@@ -91,11 +95,12 @@ static __device__ __forceinline__ bool near_cut(float zr, float zi)
 // rounding (~1e-6 rad) of an octant boundary, and then a neighbouring one, so the
 // centre stays within pi/8 + 1e-6 of the exact angle; at the branch cut (+-pi) a
 // wrong sign would move it by 2 pi instead, which the near_cut fallback rules out.
-static __device__ __forceinline__ int octant(float zr, float zi)
+template <class R>
+static __device__ __forceinline__ int octant(R zr, R zi)
 {
-    const bool steep = fabsf(zi) > fabsf(zr);
-    if (zi >= 0.f) return zr >= 0.f ? (steep ? 1 : 0) : (steep ? 2 : 3);
-    return zr >= 0.f ? (steep ? -2 : -1) : (steep ? -3 : -4);
+    const bool steep = fabs(zi) > fabs(zr);
+    if (zi >= R(0)) return zr >= R(0) ? (steep ? 1 : 0) : (steep ? 2 : 3);
+    return zr >= R(0) ? (steep ? -2 : -1) : (steep ? -3 : -4);
 }
 static __device__ __forceinline__ int octant(double a)
 {
@@ -106,14 +111,13 @@ static __device__ __forceinline__ int octant(double a)
 // Y_i(x) from a precomputed link phase V_i = (cos theta_i, sin theta_i) = conj(U_i),
 // as an octant code; the FP64 fallback recomputes from theta_i, which the caller
 // loads only then.
-template <class ThetaFn>
-static __device__ __forceinline__ int link_phase_v(float pr, float pi, float qr, float qi, float vc, float vs,
-                                                   ThetaFn theta)
+template <class R, class ThetaFn>
+static __device__ __forceinline__ int link_phase_v(R pr, R pi, R qr, R qi, R vc, R vs, ThetaFn theta)
 {
-    const float hr = vc * qr + vs * qi;   // U_i q with U_i = vc - i vs
-    const float hi = vc * qi - vs * qr;
-    const float zr = pr * hr + pi * hi;   // conj(p) U_i q
-    const float zi = pr * hi - pi * hr;
+    const R hr = vc * qr + vs * qi;   // U_i q with U_i = vc - i vs
+    const R hi = vc * qi - vs * qr;
+    const R zr = pr * hr + pi * hi;   // conj(p) U_i q
+    const R zi = pr * hi - pi * hr;
     if (near_cut(zr, zi)) return octant(link_phase_fp64(pr, pi, qr, qi, theta()));
     return octant(zr, zi);
 }
@@ -121,11 +125,11 @@ static __device__ __forceinline__ int link_phase_v(float pr, float pi, float qr,
 // [alpha]_pi from the plaquette product Q = exp(i alpha) (Eq. 15 conjugated), as an
 // octant code; the FP64 fallback recomputes alpha = a + b - c - d from the four
 // link angles.
-template <class AnglesFn>
-static __device__ __forceinline__ int wrap_from_q(float qr, float qi, AnglesFn angles)
+template <class R, class AnglesFn>
+static __device__ __forceinline__ int wrap_from_q(R qr, R qi, AnglesFn angles)
 {
     if (near_cut(qr, qi)) {
-        float a, b, c, d;
+        R a, b, c, d;
         angles(a, b, c, d);
         return octant(wrap_plaq_fp64(a, b, c, d));
     }
@@ -158,25 +162,29 @@ static __device__ __forceinline__ size_t sidx(int x, int y, int z, int N)
 }
 
 // ---------------------------------------------------------------- reduction
-struct Acc {
-    float s[NSUM];
-    float gmax;
+// per-thread sums of one tile: float32 (FP64 for the FP64 mode) along the z-march
+template <class R>
+struct AccT {
+    R s[NSUM];
+    R gmax;
     int wind, nf;
 };
+using Acc = AccT<float>;
 
-static __device__ __forceinline__ void acc_zero(Acc &a)
+template <class R>
+static __device__ __forceinline__ void acc_zero(AccT<R> &a)
 {
 #pragma unroll
-    for (int q = 0; q < NSUM; ++q) a.s[q] = 0.f;
-    a.gmax = 0.f;
+    for (int q = 0; q < NSUM; ++q) a.s[q] = R(0);
+    a.gmax = R(0);
     a.wind = 0;
     a.nf = 0;
 }
 
-// Block reduction of Acc to one row of FP64 partials: float32 within a warp,
-// FP64 across warps in a fixed order (deterministic for a fixed launch shape).
-template <int NT>
-static __device__ void block_reduce_store(Acc &a, double *out)
+// Block reduction of the sums to one row of FP64 partials: in the sums' type within
+// a warp, FP64 across warps in a fixed order (deterministic for a launch shape).
+template <int NT, class R>
+static __device__ void block_reduce_store(AccT<R> &a, double *out)
 {
     constexpr int NW = NT / 32;
     __shared__ double red[NW][NQ];
@@ -186,7 +194,7 @@ static __device__ void block_reduce_store(Acc &a, double *out)
     for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
         for (int q = 0; q < NSUM; ++q) a.s[q] += __shfl_xor_sync(0xffffffffu, a.s[q], off);
-        a.gmax = fmaxf(a.gmax, __shfl_xor_sync(0xffffffffu, a.gmax, off));
+        a.gmax = fmax(a.gmax, __shfl_xor_sync(0xffffffffu, a.gmax, off));
         a.wind += __shfl_xor_sync(0xffffffffu, a.wind, off);
         a.nf += __shfl_xor_sync(0xffffffffu, a.nf, off);
     }

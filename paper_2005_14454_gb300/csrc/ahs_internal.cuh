@@ -88,10 +88,9 @@ struct StepShape {
 StepShape step_shape(int N, int tile_y, int zchunk);   // tile_y/zchunk 0: automatic
 cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, bool measure, bool store,
                         double *partials, cudaStream_t st, bool compensated = false);
-// FP64 mode (ahs_fp64.cu)
-StepShape step_shape_fp64(int N);
-cudaError_t launch_step_fp64(const StepPtrs64 &p, const StepCoef64 &k, int N, bool measure, bool store,
-                             double *partials, cudaStream_t st);
+// FP64 precision: the tiled step in double, 8-row tiles (sh.by must be 8)
+cudaError_t launch_step64(const StepPtrs64 &p, const StepCoef64 &k, int N, const StepShape &sh, bool measure,
+                          bool store, double *partials, cudaStream_t st);
 cudaError_t launch_init_fp64(double *pr, double *pim, int N, uint64_t seed, double sigma, cudaStream_t st);
 cudaError_t launch_reduce(const double *partials, int nblocks, const ObsScalars &sc,
                           ahs_obs_t *rec, cudaStream_t st);

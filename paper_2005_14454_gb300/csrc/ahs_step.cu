@@ -27,11 +27,32 @@
 #include "ahs_device.cuh"
 
 #include <cstddef>
+#include <type_traits>
 
 namespace eng {
 namespace {
 
-template <int BY_>
+// Storage and arithmetic type of a kernel instance: float32 (the default path) or
+// FP64 (the reference precision mode) -- its complex pair, coefficients and link
+// phases (the polynomial link_sincos in float32, the library sincos in FP64).
+template <class R>
+struct Real;
+template <>
+struct Real<float> {
+    using V2 = float2;
+    using Coef = StepCoef;
+    static __device__ __forceinline__ float2 v2(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ void link(float th, float &s, float &c) { link_sincos(th, s, c); }
+};
+template <>
+struct Real<double> {
+    using V2 = double2;
+    using Coef = StepCoef64;
+    static __device__ __forceinline__ double2 v2(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ void link(double th, double &s, double &c) { sincos(th, &s, &c); }
+};
+
+template <int BY_, class R = float>
 struct Tile {
     static constexpr int BX = 32, BY = BY_, NT = BX * BY;
     static constexpr int RX = BX + 2, RY = BY + 2, NR = RX * RY;  // links/phi: [-1, BX] x [-1, BY]
@@ -41,15 +62,16 @@ struct Tile {
     static constexpr int NHB = BX + BY;                            // backward ring sites of phase B
     static_assert(NHA <= NT && NHB <= NT, "ring items must fit one pass of the CTA");
 
+    using V2 = typename Real<R>::V2;
     struct Plane {
-        float2 vx[NR], vy[NR], vz[NR], ph[NR];
+        V2 vx[NR], vy[NR], vz[NR], ph[NR];
     };
     struct Smem {
         Plane pl[3];
-        float sxy[NS], sxz[NS], syz[NS];
+        R sxy[NS], sxz[NS], syz[NS];
         // measurement steps only
         int yx[NYW], yy[NYW], yz[NYW];
-        float ex[NS], ey[NS];
+        R ex[NS], ey[NS];
     };
     static constexpr size_t kStepBytes = offsetof(Smem, yx);
     static constexpr size_t kMeasureBytes = sizeof(Smem);
@@ -59,13 +81,15 @@ struct Tile {
     static __device__ __forceinline__ int w(int ex, int ey) { return ey * YX + ex; }
 };
 
+template <class R>
 struct Raw {
-    float tx, ty, tz, pr, pi;
+    R tx, ty, tz, pr, pi;
 };
 
+template <class R>
 struct PE {
-    float qr, qi, ex, ey, ez;
-    float qrl, qil, exl, eyl, ezl;   // low words (compensated precision)
+    R qr, qi, ex, ey, ez;
+    R qrl, qil, exl, eyl, ezl;   // low words (compensated precision)
 };
 
 __device__ __forceinline__ int wrapN(int v, int N)
@@ -83,6 +107,7 @@ __device__ __forceinline__ int wrapN(int v, int N)
 enum { FPR = 0, FPI, FQR, FQI, FTX, FTY, FTZ, FEX, FEY, FEZ, FQRL, FQIL, FEXL, FEYL, FEZL };
 
 struct ParamFields {
+    using real = float;
     const StepPtrs &P;
     __device__ __forceinline__ float in(int f, uint32_t o) const
     {
@@ -101,6 +126,7 @@ struct ParamFields {
 };
 
 struct ArenaFields {
+    using real = float;
     const float *base;       // the member's first plane (buffer 0, Re phi)
     uint32_t in0, out0, V;   // plane offsets of the read and write buffers, plane size
     __device__ __forceinline__ float in(int f, uint32_t o) const { return __ldg(base + (in0 + (uint32_t)f * V + o)); }
@@ -110,10 +136,28 @@ struct ArenaFields {
     }
 };
 
+// the twenty FP64 planes of a single lattice in FP64 precision (no low words)
+struct ParamFields64 {
+    using real = double;
+    const StepPtrs64 &P;
+    __device__ __forceinline__ double in(int f, uint32_t o) const
+    {
+        const double *p = f == FPR ? P.pr : f == FPI ? P.pim : f == FQR ? P.qr : f == FQI ? P.qi : f == FTX ? P.tx
+                        : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : P.ez;
+        return __ldg(p + o);
+    }
+    __device__ __forceinline__ void out(int f, uint32_t o, double v) const
+    {
+        double *p = f == FPR ? P.pr1 : f == FPI ? P.pim1 : f == FQR ? P.qr1 : f == FQI ? P.qi1 : f == FTX ? P.tx1
+                  : f == FTY ? P.ty1 : f == FTZ ? P.tz1 : f == FEX ? P.ex1 : f == FEY ? P.ey1 : P.ez1;
+        p[o] = v;
+    }
+};
+
 template <class FA>
-__device__ __forceinline__ Raw load_raw(const FA &P, uint32_t o)
+__device__ __forceinline__ Raw<typename FA::real> load_raw(const FA &P, uint32_t o)
 {
-    Raw a;
+    Raw<typename FA::real> a;
     a.tx = P.in(FTX, o);
     a.ty = P.in(FTY, o);
     a.tz = P.in(FTZ, o);
@@ -123,22 +167,22 @@ __device__ __forceinline__ Raw load_raw(const FA &P, uint32_t o)
 }
 
 template <bool COMP, class FA>
-__device__ __forceinline__ PE load_pe(const FA &P, uint32_t o)
+__device__ __forceinline__ PE<typename FA::real> load_pe(const FA &P, uint32_t o)
 {
-    PE a;
+    PE<typename FA::real> a;
     a.qr = P.in(FQR, o);
     a.qi = P.in(FQI, o);
     a.ex = P.in(FEX, o);
     a.ey = P.in(FEY, o);
     a.ez = P.in(FEZ, o);
-    if (COMP) {
+    if constexpr (COMP) {
         a.qrl = P.in(FQRL, o);
         a.qil = P.in(FQIL, o);
         a.exl = P.in(FEXL, o);
         a.eyl = P.in(FEYL, o);
         a.ezl = P.in(FEZL, o);
     } else {
-        a.qrl = a.qil = a.exl = a.eyl = a.ezl = 0.f;
+        a.qrl = a.qil = a.exl = a.eyl = a.ezl = 0;
     }
     return a;
 }
@@ -169,8 +213,18 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
 // Q = V_i(x) conj(V_j(x)) * V_j(x+i) conj(V_i(x+j))
-__device__ __forceinline__ float2 plaquette(float2 vi, float2 vj, float2 vjp, float2 vip)
+template <class V2>
+__device__ __forceinline__ V2 plaquette(V2 vi, V2 vj, V2 vjp, V2 vip)
 {
     return cmul(cmulc(vi, vj), cmulc(vjp, vip));
 }
@@ -181,10 +235,13 @@ __device__ __forceinline__ int next_plane(int z, int N) { return z + 1 == N ? 0 
 // CTA call it together (it contains CTA barriers); with MEASURE the CTA's FP64
 // partial sums go to `partial_row`.
 template <int BY, bool MEASURE, bool STORE, bool COMP, class FA>
-__device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &P, const StepCoef &k, int N,
+__device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::Smem &S, const FA &P,
+                                          const typename Real<typename FA::real>::Coef &k, int N,
                                           int x0, int y0, int z0, int zend, double *partial_row)
 {
-    using T = Tile<BY>;
+    using R = typename FA::real;
+    using V2 = typename Real<R>::V2;
+    using T = Tile<BY, R>;
     const int tx = threadIdx.x, ty = threadIdx.y, t = tx + 32 * ty;
     const uint32_t NN = (uint32_t)N * (uint32_t)N;
 
@@ -215,15 +272,15 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
     const uint32_t cxpoff = (uint32_t)wrapN(cx + 1, N) + (uint32_t)N * (uint32_t)cy;
     const uint32_t cypoff = (uint32_t)cx + (uint32_t)N * (uint32_t)wrapN(cy + 1, N);
 
-    auto phaseA = [&](const Raw &a, int ri, typename T::Plane &pl) {
-        float s, c;
-        link_sincos(a.tx, s, c);
-        pl.vx[ri] = make_float2(c, s);
-        link_sincos(a.ty, s, c);
-        pl.vy[ri] = make_float2(c, s);
-        link_sincos(a.tz, s, c);
-        pl.vz[ri] = make_float2(c, s);
-        pl.ph[ri] = make_float2(a.pr, a.pi);
+    auto phaseA = [&](const Raw<R> &a, int ri, typename T::Plane &pl) {
+        R s, c;
+        Real<R>::link(a.tx, s, c);
+        pl.vx[ri] = Real<R>::v2(c, s);
+        Real<R>::link(a.ty, s, c);
+        pl.vy[ri] = Real<R>::v2(c, s);
+        Real<R>::link(a.tz, s, c);
+        pl.vz[ri] = Real<R>::v2(c, s);
+        pl.ph[ri] = Real<R>::v2(a.pr, a.pi);
     };
 
     // plane indices (wrapped) of zz, zz+1, zz+2, maintained incrementally
@@ -232,23 +289,23 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
     int z2 = next_plane(z1, N);
 
     // ---------------------------------------------------------------- prologue
-    Raw rc = load_raw(P, (uint32_t)zc * NN + coff);
-    Raw rh = hasA ? load_raw(P, (uint32_t)zc * NN + haoff) : Raw{};
+    Raw<R> rc = load_raw(P, (uint32_t)zc * NN + coff);
+    Raw<R> rh = hasA ? load_raw(P, (uint32_t)zc * NN + haoff) : Raw<R>{};
     phaseA(rc, T::r(tx, ty), S.pl[0]);
     if (hasA) phaseA(rh, T::r(hax, hay), S.pl[0]);
-    float thx = rc.tx, thy = rc.ty, thz = rc.tz;   // own theta of plane zz
+    R thx = rc.tx, thy = rc.ty, thz = rc.tz;   // own theta of plane zz
     rc = load_raw(P, (uint32_t)z1 * NN + coff);
     if (hasA) rh = load_raw(P, (uint32_t)z1 * NN + haoff);
-    PE pe_next{}, pe_cur{};
-    float ezPrev = 0.f;
+    PE<R> pe_next{}, pe_cur{};
+    R ezPrev = 0;
     if (MEASURE) ezPrev = P.in(FEZ, (uint32_t)zc * NN + coff);
 
     // carried from plane zz-1 (own column)
-    float2 phPrev = make_float2(0.f, 0.f), vzPrev = make_float2(1.f, 0.f);
-    float sxzPrev = 0.f, syzPrev = 0.f;
+    V2 phPrev = Real<R>::v2(0, 0), vzPrev = Real<R>::v2(1, 0);
+    R sxzPrev = 0, syzPrev = 0;
     int YxCar = 0, YyCar = 0;   // octant codes of Y_x, Y_y of plane zz (measurement)
 
-    Acc acc;
+    AccT<R> acc;
     if (MEASURE) acc_zero(acc);
 
     int b = 0;   // plane buffer holding plane zz
@@ -260,7 +317,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
         // ---- A: link phases and phi of plane zz+1
         phaseA(rc, T::r(tx, ty), pn);
         if (hasA) phaseA(rh, T::r(hax, hay), pn);
-        const float nthx = rc.tx, nthy = rc.ty, nthz = rc.tz;
+        const R nthx = rc.tx, nthy = rc.ty, nthz = rc.tz;
         if (zz + 2 <= zend) {
             rc = load_raw(P, o2 + coff);
             if (hasA) rh = load_raw(P, o2 + haoff);
@@ -271,10 +328,10 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
 
         // ---- B: plaquettes of plane zz (tile + backward ring)
         const int r0 = T::r(tx, ty), rxp = T::r(tx + 1, ty), ryp = T::r(tx, ty + 1);
-        const float2 vx0 = pc.vx[r0], vy0 = pc.vy[r0], vz0 = pc.vz[r0];
-        const float2 Qxy = plaquette(vx0, vy0, pc.vy[rxp], pc.vx[ryp]);
-        const float2 Qxz = plaquette(vx0, vz0, pc.vz[rxp], pn.vx[r0]);
-        const float2 Qyz = plaquette(vy0, vz0, pc.vz[ryp], pn.vy[r0]);
+        const V2 vx0 = pc.vx[r0], vy0 = pc.vy[r0], vz0 = pc.vz[r0];
+        const V2 Qxy = plaquette(vx0, vy0, pc.vy[rxp], pc.vx[ryp]);
+        const V2 Qxz = plaquette(vx0, vz0, pc.vz[rxp], pn.vx[r0]);
+        const V2 Qyz = plaquette(vy0, vz0, pc.vz[ryp], pn.vy[r0]);
         {
             const int qi0 = T::q(tx, ty);
             S.sxy[qi0] = Qxy.y;
@@ -283,7 +340,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
         }
         if (hasB) {
             const int rb = T::r(hbx, hby), rbx = T::r(hbx + 1, hby), rby = T::r(hbx, hby + 1);
-            const float2 bx = pc.vx[rb], by = pc.vy[rb], bz = pc.vz[rb];
+            const V2 bx = pc.vx[rb], by = pc.vy[rb], bz = pc.vz[rb];
             const int qh = T::q(hbx, hby);
             S.sxy[qh] = plaquette(bx, by, pc.vy[rbx], pc.vx[rby]).y;
             if (ringRow) S.syz[qh] = plaquette(by, bz, pc.vz[rby], pn.vy[rb]).y;
@@ -293,25 +350,25 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
             // link phases Y_i of plane zz on the tile (Y_x, Y_y carried from the
             // previous plane) and on its forward ring; old E of the backward ring
             const int wi = T::w(tx, ty);
-            const float2 p0 = pc.ph[r0], pz = pn.ph[r0];
+            const V2 p0 = pc.ph[r0], pz = pn.ph[r0];
             S.yx[wi] = YxCar;
             S.yy[wi] = YyCar;
-            const float tz0 = thz;
+            const R tz0 = thz;
             S.yz[wi] = link_phase_v(p0.x, p0.y, pz.x, pz.y, vz0.x, vz0.y, [&] { return tz0; });
             S.ex[T::q(tx, ty)] = pe_cur.ex;
             S.ey[T::q(tx, ty)] = pe_cur.ey;
             if (hasB) {
                 const int rh0 = T::r(hyx, hyy), wh = T::w(hyx, hyy);
                 const uint32_t ho = oc + hyoff;
-                const float2 hp = pc.ph[rh0];
+                const V2 hp = pc.ph[rh0];
                 if (ringRow) {   // row BY: Y_x
-                    const float2 q = pc.ph[T::r(hyx + 1, hyy)], v = pc.vx[rh0];
+                    const V2 q = pc.ph[T::r(hyx + 1, hyy)], v = pc.vx[rh0];
                     S.yx[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTX, ho); });
                 } else {         // column BX: Y_y
-                    const float2 q = pc.ph[T::r(hyx, hyy + 1)], v = pc.vy[rh0];
+                    const V2 q = pc.ph[T::r(hyx, hyy + 1)], v = pc.vy[rh0];
                     S.yy[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTY, ho); });
                 }
-                const float2 q = pn.ph[rh0], v = pc.vz[rh0];
+                const V2 q = pn.ph[rh0], v = pc.vz[rh0];
                 S.yz[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTZ, ho); });
                 if (ringRow) S.ey[T::q(hbx, hby)] = P.in(FEY, oc + hboff);
                 else S.ex[T::q(hbx, hby)] = P.in(FEX, oc + hboff);
@@ -323,47 +380,47 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
         // (ragged-tile columns too: they are the periodic images the ring reads)
         int YxNext = 0, YyNext = 0;
         if (MEASURE) {
-            const float2 pn0 = pn.ph[r0], vxn = pn.vx[r0], vyn = pn.vy[r0];
-            const float2 qxn = pn.ph[rxp], qyn = pn.ph[ryp];
-            const float tnx = nthx, tny = nthy;
+            const V2 pn0 = pn.ph[r0], vxn = pn.vx[r0], vyn = pn.vy[r0];
+            const V2 qxn = pn.ph[rxp], qyn = pn.ph[ryp];
+            const R tnx = nthx, tny = nthy;
             YxNext = link_phase_v(pn0.x, pn0.y, qxn.x, qxn.y, vxn.x, vxn.y, [&] { return tnx; });
             YyNext = link_phase_v(pn0.x, pn0.y, qyn.x, qyn.y, vyn.x, vyn.y, [&] { return tny; });
         }
 
         // ---- C: kick and drift of plane zz
-        const float2 p0 = pc.ph[r0];
+        const V2 p0 = pc.ph[r0];
         if (zz >= z0 && valid) {
             const int rxm = T::r(tx - 1, ty), rym = T::r(tx, ty - 1);
             // forward hops U_i(x) phi(x+i) = conj(V_i) phi(x+i)
-            const float2 hx = cmulc(pc.ph[rxp], vx0);
-            const float2 hy = cmulc(pc.ph[ryp], vy0);
-            const float2 hz = cmulc(pn.ph[r0], vz0);
+            const V2 hx = cmulc(pc.ph[rxp], vx0);
+            const V2 hy = cmulc(pc.ph[ryp], vy0);
+            const V2 hz = cmulc(pn.ph[r0], vz0);
             // backward hops U_i(x-i)^* phi(x-i) = V_i(x-i) phi(x-i)
-            const float2 bxh = cmul(pc.vx[rxm], pc.ph[rxm]);
-            const float2 byh = cmul(pc.vy[rym], pc.ph[rym]);
-            const float2 bzh = cmul(vzPrev, phPrev);
-            const float hsr = ((hx.x + bxh.x) + (hy.x + byh.x)) + (hz.x + bzh.x);
-            const float hsi = ((hx.y + bxh.y) + (hy.y + byh.y)) + (hz.y + bzh.y);
-            const float mod2 = p0.x * p0.x + p0.y * p0.y;
-            const float potf = k.kpi_pot * (mod2 - k.sigma2);
-            float qnr, qni, qnrl = 0.f, qnil = 0.f;
-            if (COMP) {
+            const V2 bxh = cmul(pc.vx[rxm], pc.ph[rxm]);
+            const V2 byh = cmul(pc.vy[rym], pc.ph[rym]);
+            const V2 bzh = cmul(vzPrev, phPrev);
+            const R hsr = ((hx.x + bxh.x) + (hy.x + byh.x)) + (hz.x + bzh.x);
+            const R hsi = ((hx.y + bxh.y) + (hy.y + byh.y)) + (hz.y + bzh.y);
+            const R mod2 = p0.x * p0.x + p0.y * p0.y;
+            const R potf = k.kpi_pot * (mod2 - k.sigma2);
+            R qnr, qni, qnrl = 0, qnil = 0;
+            if constexpr (COMP) {
                 comp_update(k.cpi, pe_cur.qr, pe_cur.qrl, k.kpi_lap * (hsr - 6.f * p0.x) - potf * p0.x, qnr, qnrl);
                 comp_update(k.cpi, pe_cur.qi, pe_cur.qil, k.kpi_lap * (hsi - 6.f * p0.y) - potf * p0.y, qni, qnil);
             } else {
-                qnr = k.cpi * pe_cur.qr + k.kpi_lap * (hsr - 6.f * p0.x) - potf * p0.x;
-                qni = k.cpi * pe_cur.qi + k.kpi_lap * (hsi - 6.f * p0.y) - potf * p0.y;
+                qnr = k.cpi * pe_cur.qr + k.kpi_lap * (hsr - R(6) * p0.x) - potf * p0.x;
+                qni = k.cpi * pe_cur.qi + k.kpi_lap * (hsi - R(6) * p0.y) - potf * p0.y;
             }
             // currents J_i = Im(conj(phi) U_i phi(x+i))
-            const float jx = p0.x * hx.y - p0.y * hx.x;
-            const float jy = p0.x * hy.y - p0.y * hy.x;
-            const float jz = p0.x * hz.y - p0.y * hz.x;
-            const float sxy = Qxy.y, sxz = Qxz.y, syz = Qyz.y;
-            const float cxv = -(sxy - S.sxy[T::q(tx, ty - 1)]) - (sxz - sxzPrev);
-            const float cyv = (sxy - S.sxy[T::q(tx - 1, ty)]) - (syz - syzPrev);
-            const float czv = (sxz - S.sxz[T::q(tx - 1, ty)]) + (syz - S.syz[T::q(tx, ty - 1)]);
-            float enx, eny, enz, enxl = 0.f, enyl = 0.f, enzl = 0.f;
-            if (COMP) {
+            const R jx = p0.x * hx.y - p0.y * hx.x;
+            const R jy = p0.x * hy.y - p0.y * hy.x;
+            const R jz = p0.x * hz.y - p0.y * hz.x;
+            const R sxy = Qxy.y, sxz = Qxz.y, syz = Qyz.y;
+            const R cxv = -(sxy - S.sxy[T::q(tx, ty - 1)]) - (sxz - sxzPrev);
+            const R cyv = (sxy - S.sxy[T::q(tx - 1, ty)]) - (syz - syzPrev);
+            const R czv = (sxz - S.sxz[T::q(tx - 1, ty)]) + (syz - S.syz[T::q(tx, ty - 1)]);
+            R enx, eny, enz, enxl = 0, enyl = 0, enzl = 0;
+            if constexpr (COMP) {
                 comp_update(k.ce, pe_cur.ex, pe_cur.exl, k.ke_curl * cxv + k.ke_cur * jx, enx, enxl);
                 comp_update(k.ce, pe_cur.ey, pe_cur.eyl, k.ke_curl * cyv + k.ke_cur * jy, eny, enyl);
                 comp_update(k.ce, pe_cur.ez, pe_cur.ezl, k.ke_curl * czv + k.ke_cur * jz, enz, enzl);
@@ -374,41 +431,42 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
             }
 
             if (MEASURE) {
-                const float pbr = COMP ? 0.5f * ((pe_cur.qr + qnr) + (pe_cur.qrl + qnrl)) : 0.5f * (pe_cur.qr + qnr);
-                const float pbi = COMP ? 0.5f * ((pe_cur.qi + qni) + (pe_cur.qil + qnil)) : 0.5f * (pe_cur.qi + qni);
-                const float K = pbr * pbr + pbi * pbi;
-                const float gxr = hx.x - p0.x, gxi = hx.y - p0.y, gyr = hy.x - p0.x, gyi = hy.y - p0.y;
-                const float gzr = hz.x - p0.x, gzi = hz.y - p0.y;
-                const float G = k.m_grad * ((gxr * gxr + gxi * gxi) + (gyr * gyr + gyi * gyi) + (gzr * gzr + gzi * gzi));
-                const float dm = mod2 - k.sigma2;
-                const float V = k.m_pot * dm * dm;
-                const float ebx = COMP ? 0.5f * ((pe_cur.ex + enx) + (pe_cur.exl + enxl)) : 0.5f * (pe_cur.ex + enx);
-                const float eby = COMP ? 0.5f * ((pe_cur.ey + eny) + (pe_cur.eyl + enyl)) : 0.5f * (pe_cur.ey + eny);
-                const float ebz = COMP ? 0.5f * ((pe_cur.ez + enz) + (pe_cur.ezl + enzl)) : 0.5f * (pe_cur.ez + enz);
-                const float El = k.m_el * (ebx * ebx + eby * eby + ebz * ebz);
-                const float B = k.m_mag * ((1.f - Qxy.x) + (1.f - Qxz.x) + (1.f - Qyz.x));
-                const float L = K - G - V + El - B;
-                const float rho = K + G + V + El + B;
-                const float pres = K - G * (1.f / 3.f) - V + (El + B) * (1.f / 3.f);
-                const float div = ((pe_cur.ex - S.ex[T::q(tx - 1, ty)]) + (pe_cur.ey - S.ey[T::q(tx, ty - 1)]) +
-                                   (pe_cur.ez - ezPrev)) * k.inv_dx;
-                const float g = div - k.m_gauss * (p0.x * pe_cur.qi - p0.y * pe_cur.qr);
+                const R half = R(0.5), third = R(1) / R(3);
+                const R pbr = COMP ? half * ((pe_cur.qr + qnr) + (pe_cur.qrl + qnrl)) : half * (pe_cur.qr + qnr);
+                const R pbi = COMP ? half * ((pe_cur.qi + qni) + (pe_cur.qil + qnil)) : half * (pe_cur.qi + qni);
+                const R K = pbr * pbr + pbi * pbi;
+                const R gxr = hx.x - p0.x, gxi = hx.y - p0.y, gyr = hy.x - p0.x, gyi = hy.y - p0.y;
+                const R gzr = hz.x - p0.x, gzi = hz.y - p0.y;
+                const R G = k.m_grad * ((gxr * gxr + gxi * gxi) + (gyr * gyr + gyi * gyi) + (gzr * gzr + gzi * gzi));
+                const R dm = mod2 - k.sigma2;
+                const R V = k.m_pot * dm * dm;
+                const R ebx = COMP ? half * ((pe_cur.ex + enx) + (pe_cur.exl + enxl)) : half * (pe_cur.ex + enx);
+                const R eby = COMP ? half * ((pe_cur.ey + eny) + (pe_cur.eyl + enyl)) : half * (pe_cur.ey + eny);
+                const R ebz = COMP ? half * ((pe_cur.ez + enz) + (pe_cur.ezl + enzl)) : half * (pe_cur.ez + enz);
+                const R El = k.m_el * (ebx * ebx + eby * eby + ebz * ebz);
+                const R B = k.m_mag * ((R(1) - Qxy.x) + (R(1) - Qxz.x) + (R(1) - Qyz.x));
+                const R L = K - G - V + El - B;
+                const R rho = K + G + V + El + B;
+                const R pres = K - G * third - V + (El + B) * third;
+                const R div = ((pe_cur.ex - S.ex[T::q(tx - 1, ty)]) + (pe_cur.ey - S.ey[T::q(tx, ty - 1)]) +
+                               (pe_cur.ez - ezPrev)) * k.inv_dx;
+                const R g = div - k.m_gauss * (p0.x * pe_cur.qi - p0.y * pe_cur.qr);
                 acc.s[Q_K] += K; acc.s[Q_G] += G; acc.s[Q_V] += V; acc.s[Q_EL] += El; acc.s[Q_B] += B;
                 acc.s[Q_L] += L; acc.s[Q_KL] += K * L; acc.s[Q_GL] += G * L; acc.s[Q_PL] += pres * L;
                 acc.s[Q_RL] += rho * L; acc.s[Q_G2] += g * g;
-                acc.gmax = fmaxf(acc.gmax, fabsf(g));
+                acc.gmax = fmax(acc.gmax, fabs(g));
                 if (!isfinite(rho) || !isfinite(L) || !isfinite(g)) acc.nf += 1;
 
                 // plaquette windings with lower corner x
                 const int wi = T::w(tx, ty);
                 const int Yx = YxCar, Yy = YyCar, Yz = S.yz[wi];
-                const float tnx = nthx, tny = nthy;
-                const float t0x = thx, t0y = thy, t0z = thz;
-                const int wxy = wrap_from_q(Qxy.x, Qxy.y, [&](float &a, float &bb, float &c, float &d) {
+                const R tnx = nthx, tny = nthy;
+                const R t0x = thx, t0y = thy, t0z = thz;
+                const int wxy = wrap_from_q(Qxy.x, Qxy.y, [&](R &a, R &bb, R &c, R &d) {
                     a = t0x; bb = P.in(FTY, oc + cxpoff); c = P.in(FTX, oc + cypoff); d = t0y; });
-                const int wxz = wrap_from_q(Qxz.x, Qxz.y, [&](float &a, float &bb, float &c, float &d) {
+                const int wxz = wrap_from_q(Qxz.x, Qxz.y, [&](R &a, R &bb, R &c, R &d) {
                     a = t0x; bb = P.in(FTZ, oc + cxpoff); c = tnx; d = t0z; });
-                const int wyz = wrap_from_q(Qyz.x, Qyz.y, [&](float &a, float &bb, float &c, float &d) {
+                const int wyz = wrap_from_q(Qyz.x, Qyz.y, [&](R &a, R &bb, R &c, R &d) {
                     a = t0y; bb = P.in(FTZ, oc + cypoff); c = tny; d = t0z; });
                 const int nxy = winding(Yx, S.yy[T::w(tx + 1, ty)], S.yx[T::w(tx, ty + 1)], Yy, wxy);
                 const int nxz = winding(Yx, S.yz[T::w(tx + 1, ty)], YxNext, Yz, wxz);
@@ -425,20 +483,26 @@ __device__ __forceinline__ void tile_step(typename Tile<BY>::Smem &S, const FA &
                 P.out(FEZ, o, enz);
                 P.out(FPR, o, p0.x + k.dphi * (COMP ? qnr + qnrl : qnr));
                 P.out(FPI, o, p0.y + k.dphi * (COMP ? qni + qnil : qni));
-                if (COMP) {
+                if constexpr (COMP) {
                     P.out(FQRL, o, qnrl);
                     P.out(FQIL, o, qnil);
                     P.out(FEXL, o, enxl);
                     P.out(FEYL, o, enyl);
                     P.out(FEZL, o, enzl);
                 }
-                float t1x = thx + k.dtheta * (COMP ? enx + enxl : enx);
-                float t1y = thy + k.dtheta * (COMP ? eny + enyl : eny);
-                float t1z = thz + k.dtheta * (COMP ? enz + enzl : enz);
+                R t1x = thx + k.dtheta * (COMP ? enx + enxl : enx);
+                R t1y = thy + k.dtheta * (COMP ? eny + enyl : eny);
+                R t1z = thz + k.dtheta * (COMP ? enz + enzl : enz);
                 if (k.wrap) {
-                    t1x += kTwoPiF * floorf((kPiF - t1x) * kInvTwoPiF);
-                    t1y += kTwoPiF * floorf((kPiF - t1y) * kInvTwoPiF);
-                    t1z += kTwoPiF * floorf((kPiF - t1z) * kInvTwoPiF);
+                    if constexpr (std::is_same<R, float>::value) {
+                        t1x += kTwoPiF * floorf((kPiF - t1x) * kInvTwoPiF);
+                        t1y += kTwoPiF * floorf((kPiF - t1y) * kInvTwoPiF);
+                        t1z += kTwoPiF * floorf((kPiF - t1z) * kInvTwoPiF);
+                    } else {
+                        t1x += 2.0 * kPiD * floor((kPiD - t1x) / (2.0 * kPiD));
+                        t1y += 2.0 * kPiD * floor((kPiD - t1y) / (2.0 * kPiD));
+                        t1z += 2.0 * kPiD * floor((kPiD - t1z) / (2.0 * kPiD));
+                    }
                 }
                 P.out(FTX, o, t1x);
                 P.out(FTY, o, t1y);
@@ -481,6 +545,21 @@ __global__ void __launch_bounds__(32 * BY, (MEASURE ? 16 : 32) / BY)
 // and runs them; the list is ordered by the members' last step, so at step n the
 // tiles of members still running form the prefix live[n].  The member's field
 // base and coefficients are staged per tile.
+// FP64 precision: the same tile march in double (8-row tiles; two CTAs per SM for
+// a plain step, one for a measuring step).
+template <bool MEASURE, bool STORE>
+__global__ void __launch_bounds__(256, MEASURE ? 1 : 2)
+    step_tiled64(StepPtrs64 P, StepCoef64 k, int N, int Dz, double *partials)
+{
+    using T = Tile<8, double>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
+    const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * 8, z0 = blockIdx.z * Dz;
+    const size_t bi = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+    tile_step<8, MEASURE, STORE, false>(S, ParamFields64{P}, k, N, x0, y0, z0, min(z0 + Dz, N),
+                                        MEASURE ? partials + bi * NQ : nullptr);
+}
+
 template <int BY, bool MEASURE>
 __global__ void __launch_bounds__(32 * BY, (MEASURE ? 16 : 32) / BY) batch_step(BatchLaunch L, int dn)
 {
@@ -558,6 +637,26 @@ cudaError_t launch_variant(const StepPtrs &p, const StepCoef &k, int N, int Dz, 
     return cudaGetLastError();
 }
 
+template <bool M, bool S>
+cudaError_t launch_variant64(const StepPtrs64 &p, const StepCoef64 &k, int N, int Dz, double *partials,
+                             cudaStream_t st)
+{
+    using T = Tile<8, double>;
+    const size_t bytes = M ? T::kMeasureBytes : T::kStepBytes;
+    static int configured_device = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured_device != dev) {
+        e = cudaFuncSetAttribute(step_tiled64<M, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        configured_device = dev;
+    }
+    dim3 grid((N + 31) / 32, (N + 7) / 8, (N + Dz - 1) / Dz);
+    step_tiled64<M, S><<<grid, dim3(32, 8), bytes, st>>>(p, k, N, Dz, partials);
+    return cudaGetLastError();
+}
+
 template <int BY, bool C>
 cudaError_t launch_by(const StepPtrs &p, const StepCoef &k, int N, int Dz, bool measure, bool store,
                       double *partials, cudaStream_t st)
@@ -607,6 +706,16 @@ cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepS
     }
     if (sh.by == 16) return launch_by<16, false>(p, k, N, sh.dz, measure, store, partials, st);
     return launch_by<8, false>(p, k, N, sh.dz, measure, store, partials, st);
+}
+
+cudaError_t launch_step64(const StepPtrs64 &p, const StepCoef64 &k, int N, const StepShape &sh, bool measure,
+                          bool store, double *partials, cudaStream_t st)
+{
+    if (sh.by != 8) return cudaErrorInvalidValue;
+    if (measure && store) return launch_variant64<true, true>(p, k, N, sh.dz, partials, st);
+    if (measure) return launch_variant64<true, false>(p, k, N, sh.dz, partials, st);
+    if (store) return launch_variant64<false, true>(p, k, N, sh.dz, partials, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace eng
