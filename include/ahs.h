@@ -237,6 +237,10 @@ int ahs_batch_init(ahs_batch_t *b);
 int ahs_batch_run(ahs_batch_t *b, int max_steps);
 /* measurement log of member m (as ahs_records) */
 int ahs_batch_records(ahs_batch_t *b, int m, ahs_obs_t *out, int max);
+/* measure member m at its current time level without changing it (as ahs_measure:
+ * the member's launch shape, a record equal to the one a single lattice of the
+ * same launch shape reports); synchronous on the batch's stream */
+int ahs_batch_measure(ahs_batch_t *b, int m, ahs_obs_t *out);
 /* fields of member m at its current time (as ahs_fields / ahs_set_fields) */
 int ahs_batch_fields(ahs_batch_t *b, int m, int which, void *host_dst, size_t bytes);
 int ahs_batch_set_fields(ahs_batch_t *b, int m, int which, const void *host_src, size_t bytes);

@@ -175,6 +175,9 @@ class Batch:
     def step_info(self, m: int):
         return _abi.ahs_batch_step_info(self.b, m)
 
+    def measure(self, m: int) -> dict:
+        return _abi.ahs_batch_measure(self.b, m)
+
     def set_option(self, key: int, value: float):
         _abi.ahs_batch_set_option(self.b, key, value)
 

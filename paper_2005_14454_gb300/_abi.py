@@ -34,7 +34,7 @@ EXPORTS = (
     "ahs_batch_create", "ahs_batch_init", "ahs_batch_run", "ahs_batch_records", "ahs_batch_fields",
     "ahs_batch_set_fields", "ahs_batch_step_info", "ahs_batch_set_option", "ahs_batch_get_option",
     "ahs_batch_member_zchunk", "ahs_batch_autotune", "ahs_batch_kernel_time", "ahs_batch_set_stream",
-    "ahs_batch_destroy",
+    "ahs_batch_destroy", "ahs_batch_measure",
 )
 _NON_INT = ("ahs_create", "ahs_destroy", "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs",
             "ahs_batch_create", "ahs_batch_destroy")
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ahs_batch_init.argtypes = [H]
     L.ahs_batch_run.argtypes = [H, i]
     L.ahs_batch_records.argtypes = [H, i, ctypes.POINTER(ahs_obs_t), i]
+    L.ahs_batch_measure.argtypes = [H, i, ctypes.POINTER(ahs_obs_t)]
     L.ahs_batch_fields.argtypes = [H, i, i, vp, sz]
     L.ahs_batch_set_fields.argtypes = [H, i, i, vp, sz]
     L.ahs_batch_step_info.argtypes = [H, i, i64p, i64p]
@@ -262,6 +263,12 @@ def ahs_batch_init(b):
 
 def ahs_batch_run(b, max_steps):
     return check(lib().ahs_batch_run(b, max_steps), "ahs_batch_run")
+
+
+def ahs_batch_measure(b, m) -> dict:
+    o = ahs_obs_t()
+    check(lib().ahs_batch_measure(b, m, ctypes.byref(o)), "ahs_batch_measure")
+    return o.as_dict()
 
 
 def ahs_batch_records(b, m):

@@ -81,6 +81,11 @@ struct ahs_batch {
     cudaGraphExec_t gexec = nullptr;
     bool graph_dirty = true;
 
+    // on-demand measurement of one member (ahs_batch_measure)
+    double *d_mpart = nullptr;
+    int mpart_rows = 0;
+    ahs_obs_t *d_mrec = nullptr, *h_mrec = nullptr;
+
     int64_t n = 0;
     bool ready = false;
     std::vector<std::vector<ahs_obs_t>> log;
@@ -390,6 +395,9 @@ void ahs_batch_destroy(ahs_batch_t *b)
     free_tables(b);
     cudaFree(b->d_counter);
     cudaFree(b->arena);
+    cudaFree(b->d_mpart);
+    cudaFree(b->d_mrec);
+    if (b->h_mrec) cudaFreeHost(b->h_mrec);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -525,6 +533,36 @@ int ahs_batch_set_fields(ahs_batch_t *b, int m, int which, const void *src, size
         BCU(cudaMemcpyAsync(b->plane(m, cur, first + i), (const float *)src + (size_t)i * V, sizeof(float) * V,
                             cudaMemcpyHostToDevice, b->stream));
     BCU(cudaStreamSynchronize(b->stream));
+    return report_ok();
+}
+
+int ahs_batch_measure(ahs_batch_t *b, int m, ahs_obs_t *out)
+{
+    if (int r = check_member(b, m)) return r;
+    if (!out) return bfail(AHS_EINVAL, "null output record");
+    if (!b->ready) return bfail(AHS_ESTATE, "batch not initialised");
+    BCU(cudaSetDevice(b->device));
+    const LatticeParams &P = b->prm[m];
+    const int64_t t = b->member_time(m);
+    const StepShape sh = step_shape(P.N, b->by, b->dz[m]);
+    BCU(cudaStreamSynchronize(b->stream));
+    if (sh.blocks > b->mpart_rows) {
+        cudaFree(b->d_mpart);
+        b->d_mpart = nullptr;
+        b->mpart_rows = 0;
+        BCU(cudaMalloc(&b->d_mpart, sizeof(double) * NQ * (size_t)sh.blocks));
+        b->mpart_rows = sh.blocks;
+    }
+    if (!b->d_mrec) BCU(cudaMalloc(&b->d_mrec, sizeof(ahs_obs_t)));
+    if (!b->h_mrec) BCU(cudaMallocHost(&b->h_mrec, sizeof(ahs_obs_t)));
+    // the measurement launch of a single lattice (the kick of step t kept in
+    // registers, nothing written) on the member's current buffer
+    BCU(launch_step(member_ptrs(b, m, (int)(t & 1)), coefficients(&P, t), P.N, sh, true, false, b->d_mpart,
+                    b->stream));
+    BCU(launch_reduce(b->d_mpart, sh.blocks, obs_scalars(&P, t), b->d_mrec, b->stream));
+    BCU(cudaMemcpyAsync(b->h_mrec, b->d_mrec, sizeof(ahs_obs_t), cudaMemcpyDeviceToHost, b->stream));
+    BCU(cudaStreamSynchronize(b->stream));
+    *out = *b->h_mrec;
     return report_ok();
 }
 

@@ -205,3 +205,32 @@ def test_benchmark_ensemble_128_members_match_oracle(pkg, orc):
     g, o = np.mean(gpu, axis=0), np.mean(ref, axis=0)
     for j, k in enumerate(keys):
         assert np.allclose(g[:, j], o[:, j], rtol=0.01), (k, g[:, j], o[:, j])
+
+
+def test_batch_measure_equals_single_lattice_measure(pkg):
+    """ahs_batch_measure: a member measured at its current time (mid-run, and after
+    it stopped) gives the record ahs_measure gives for the same state and launch
+    shape, and leaves the batch unchanged."""
+    from paper_2005_14454_gb300._abi import AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK, ahs_batch_member_zchunk
+    members = [(24, 1, 31, 9), (20, 2, 32, 14)]
+    N, era, seed, end = zip(*members)
+    with pkg.Batch(N, era, seed, list(end), measure_every=5, **PARAMS) as b:
+        b.init()
+        b.run(6)
+        got = [b.measure(i) for i in range(2)]
+        before = [b.state(i) for i in range(2)]
+        again = [b.measure(i) for i in range(2)]
+        assert got == again and all(np.array_equal(b.state(i), before[i]) for i in range(2))
+        b.run()
+        final = b.measure(0)
+        for i, (n, e, sd, ne) in enumerate(members):
+            with pkg.Lattice(n, era=e, measure_every=0, **PARAMS) as lat:
+                lat.set_option(AHS_OPT_TILE_Y, 8)
+                lat.set_option(AHS_OPT_ZCHUNK, ahs_batch_member_zchunk(b.b, i))
+                lat.init(sd)
+                lat.step(6)
+                assert lat.measure() == got[i], i
+                if i == 0:
+                    lat.step(ne - 6)
+                    assert lat.measure() == final
+    assert got[0]["step"] == 6 and final["step"] == 9
