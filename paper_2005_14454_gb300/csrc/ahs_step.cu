@@ -299,6 +299,8 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
     PE<R> pe_next{}, pe_cur{};
     R ezPrev = 0;
     if (MEASURE) ezPrev = P.in(FEZ, (uint32_t)zc * NN + coff);
+    // old E of this thread's backward-ring site (Gauss residual), loaded one plane ahead
+    R eRing = 0, eRingNext = 0;
 
     // carried from plane zz-1 (own column)
     V2 phPrev = Real<R>::v2(0, 0), vzPrev = Real<R>::v2(1, 0);
@@ -324,6 +326,10 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         }
         pe_cur = pe_next;
         if (zz + 1 < zend) pe_next = load_pe<COMP>(P, o1 + coff);
+        if (MEASURE) {
+            eRing = eRingNext;
+            if (hasB && zz + 1 < zend) eRingNext = P.in(ringRow ? FEY : FEX, o1 + hboff);
+        }
         __syncthreads();
 
         // ---- B: plaquettes of plane zz (tile + backward ring)
@@ -370,8 +376,8 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
                 }
                 const V2 q = pn.ph[rh0], v = pc.vz[rh0];
                 S.yz[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTZ, ho); });
-                if (ringRow) S.ey[T::q(hbx, hby)] = P.in(FEY, oc + hboff);
-                else S.ex[T::q(hbx, hby)] = P.in(FEX, oc + hboff);
+                if (ringRow) S.ey[T::q(hbx, hby)] = eRing;
+                else S.ex[T::q(hbx, hby)] = eRing;
             }
         }
         __syncthreads();
