@@ -237,3 +237,18 @@ def test_error_per_observable_against_oracle(pkg, orc):
                 continue                                 # a residual: rounding level, not relative
             assert meas_err < (1e-10 if mode == "fp64" else 2e-4), (mode, k, meas_err)
             assert run_err < (1e-8 if mode == "fp64" else 1e-2), (mode, k, run_err)
+
+
+@pytest.mark.parametrize("N", [20, 40])
+def test_fp64_fields_independent_of_zchunk(pkg, N):
+    # the FP64 step runs the tiled kernel: every z-chunk length gives the same bits
+    from paper_2005_14454_gb300._abi import AHS_OPT_ZCHUNK
+    outs = []
+    for dz in (0, 1, 3, N):
+        with pkg.Lattice(N, era=2, measure_every=4, precision="fp64", **PARAMS) as lat:
+            lat.set_option(AHS_OPT_ZCHUNK, dz)
+            lat.init(6)
+            lat.step(9)
+            outs.append((lat.state(), [r["n_wind"] for r in lat.records()]))
+    for F, w in outs[1:]:
+        assert np.array_equal(F, outs[0][0]) and w == outs[0][1]
