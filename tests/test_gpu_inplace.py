@@ -36,7 +36,8 @@ def run_pair(eng, N, steps, era=1, s=0.0, every=5, seed=3, start=None, shape=Non
     return out
 
 
-@pytest.mark.parametrize("N,era,s,steps", [(36, 1, 0.0, 25), (64, 2, 0.0, 20), (20, 0, 0.0, 31), (24, 2, 1.0, 12)])
+@pytest.mark.parametrize("N,era,s,steps", [(36, 1, 0.0, 25), (64, 2, 0.0, 20), (20, 0, 0.0, 31), (24, 2, 1.0, 12),
+                                         (5, 1, 0.0, 7)])
 def test_fields_and_records_bit_identical_to_double_buffering(eng, N, era, s, steps):
     (F0, R0, M0), (F1, R1, M1) = run_pair(eng, N, steps, era=era, s=s)
     assert np.array_equal(F0, F1)

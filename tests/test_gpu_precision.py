@@ -23,7 +23,7 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-@pytest.mark.parametrize("N,era,s", [(24, 1, 0.0), (20, 2, 1.0), (16, 0, 0.0)])
+@pytest.mark.parametrize("N,era,s", [(24, 1, 0.0), (20, 2, 1.0), (16, 0, 0.0), (5, 1, 0.0)])
 def test_fp64_matches_oracle(pkg, orc, N, era, s):
     with pkg.Lattice(N, era=era, s=s, measure_every=0, precision="fp64", **PARAMS) as lat:
         lat.init(77)
