@@ -52,6 +52,7 @@ class Lattice:
                  momenta_in_place: bool = False, core_growth=None):
         era = ERAS.get(era, era) if isinstance(era, str) else era
         self.N = N
+        self.params = dict(N=N, dx=dx, dt=dt, lambda0=lambda0, e0=e0, sigma=sigma, s=s, era=era)
         self.h = _abi.ahs_create(N, dx, dt, lambda0, e0, sigma, s, era)
         _abi.ahs_set_option(self.h, _abi.AHS_OPT_MEASURE_EVERY, measure_every)
         if precision is not None:
@@ -127,6 +128,45 @@ class Lattice:
 
     def autotune(self):
         _abi.ahs_autotune(self.h)
+
+    # checkpoint / restart ------------------------------------------------------
+    _SAVED_OPTIONS = ("AHS_OPT_STEP", "AHS_OPT_ALPHA", "AHS_OPT_TAU0", "AHS_OPT_WRAP_THETA",
+                      "AHS_OPT_MEASURE_EVERY", "AHS_OPT_PRECISION", "AHS_OPT_COOLING",
+                      "AHS_OPT_MOMENTA_IN_PLACE", "AHS_OPT_CORE_GROWTH_S", "AHS_OPT_CORE_GROWTH_TAU",
+                      "AHS_OPT_TILE_Y", "AHS_OPT_ZCHUNK")
+
+    def save(self, path: str):
+        """Write a restart file (numpy .npz): the fields at the current time level in
+        their storage precision (with the low words in compensated precision), the
+        parameters of ahs_create and every option that shapes the evolution.  A run
+        restored from it continues bit for bit (the measurement log is not saved)."""
+        import json
+        opts = {k: _abi.ahs_get_option(self.h, getattr(_abi, k)) for k in self._SAVED_OPTIONS}
+        arrays = {"fields": self.state()}
+        if int(opts["AHS_OPT_PRECISION"]) == _abi.AHS_PREC_FP32_COMPENSATED:
+            arrays["low"] = self.field(AHS_FIELD_LOW)
+        meta = json.dumps({"params": self.params, "options": opts})
+        with open(path, "wb") as f:
+            np.savez(f, meta=np.frombuffer(meta.encode(), dtype=np.uint8), **arrays)
+
+    @classmethod
+    def restore(cls, path: str, stream: int | None = None) -> "Lattice":
+        """A new lattice with the parameters, options, time level and fields of a
+        restart file written by save()."""
+        import json
+        with np.load(path) as z:
+            meta = json.loads(bytes(z["meta"]).decode())
+            fields = z["fields"]
+            low = z["low"] if "low" in z.files else None
+        lat = cls(measure_every=0, stream=stream, **meta["params"])
+        opts = meta["options"]
+        order = ["AHS_OPT_PRECISION", "AHS_OPT_MOMENTA_IN_PLACE"]   # these reallocate: first
+        for k in order + [k for k in opts if k not in order]:
+            _abi.ahs_set_option(lat.h, getattr(_abi, k), opts[k])
+        lat.set_state(fields)
+        if low is not None:
+            _abi.ahs_set_fields(lat.h, AHS_FIELD_LOW, low)
+        return lat
 
 
 class Batch:
