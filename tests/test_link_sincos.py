@@ -86,3 +86,47 @@ def test_special_angles_and_symmetry():
     s1, c1 = link_sincos(x, K)
     s2, c2 = link_sincos(-x, K)
     assert np.array_equal(s1, -s2) and np.array_equal(c1, c2)
+
+
+def constants64():
+    txt = open(os.path.join(CSRC, "ahs_device.cuh")).read()
+    arr = {k: [float(v) for v in re.findall(r"[-+0-9.eE]+", body)]
+           for k, body in re.findall(r"constexpr double (kLink[SC]64)\[8\] = \{([^}]*)\}", txt)}
+    sc = {k: float(v) for k, v in re.findall(r"constexpr double (kLink\w+64) = ([-+0-9.eE]+);", txt)}
+    return arr["kLinkS64"], arr["kLinkC64"], sc
+
+
+def test_double_polynomials_fit_and_reduction():
+    """FP64 link phases: the committed coefficients (exact arithmetic) are within
+    1e-17 (sin, relative) and 5e-17 (cos) on [0, pi/2], and the whole evaluation in FP64 (reduction,
+    polynomials, sign) within 3e-16 of the exact values for |th| up to 1e4."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    S, C, sc = constants64()
+    assert len(S) == 8 and len(C) == 8
+    assert sc["kLinkPiA64"] == np.pi and sc["kLinkInvPi64"] == 1 / np.pi
+    assert sc["kLinkPiB64"] == float(mp.pi - mp.mpf(np.pi))
+    worst_s = worst_c = 0.0
+    for i in range(400):
+        r = mp.mpf(i + 0.5) / 400 * mp.pi / 2
+        r2 = r * r
+        ps = sum(mp.mpf(S[j]) * r2 ** j for j in range(8))
+        pc = sum(mp.mpf(C[j]) * r2 ** j for j in range(8))
+        worst_s = max(worst_s, float(abs((r + r ** 3 * ps) - mp.sin(r)) / mp.sin(r)))
+        worst_c = max(worst_c, float(abs((1 + r2 * pc) - mp.cos(r))))
+    assert worst_s < 1e-17 and worst_c < 5e-17         # cos: the FP64 rounding of C0 ~ -1/2
+    th = np.random.default_rng(9).uniform(-1e4, 1e4, 3000)
+    k = np.rint(th * sc["kLinkInvPi64"])
+    # the two fused multiply-adds of the reduction, each rounded once
+    fma = lambda a, b_, c: float(mp.mpf(a) * mp.mpf(b_) + mp.mpf(c))
+    r = np.array([fma(-kk, sc["kLinkPiB64"], fma(-kk, sc["kLinkPiA64"], t)) for kk, t in zip(k, th)])
+    r2 = r * r
+    ps = np.full_like(r, S[7]); pc = np.full_like(r, C[7])
+    for j in range(6, -1, -1):
+        ps = r2 * ps + S[j]
+        pc = r2 * pc + C[j]
+    sgn = np.where(k.astype(np.int64) % 2 == 1, -1.0, 1.0)
+    s, c = sgn * (r + r * r2 * ps), sgn * (1.0 + r2 * pc)
+    es = max(abs(float(mp.mpf(a) - mp.sin(mp.mpf(t)))) for a, t in zip(s, th))
+    ec = max(abs(float(mp.mpf(a) - mp.cos(mp.mpf(t)))) for a, t in zip(c, th))
+    assert es < 3e-16 and ec < 3e-16, (es, ec)
