@@ -34,7 +34,7 @@ namespace {
 
 // Storage and arithmetic type of a kernel instance: float32 (the default path) or
 // FP64 (the reference precision mode) -- its complex pair, coefficients and link
-// phases (the polynomial link_sincos in float32, the library sincos in FP64).
+// phases (the polynomial link_sincos of that precision).
 template <class R>
 struct Real;
 template <>
@@ -49,7 +49,7 @@ struct Real<double> {
     using V2 = double2;
     using Coef = StepCoef64;
     static __device__ __forceinline__ double2 v2(double a, double b) { return make_double2(a, b); }
-    static __device__ __forceinline__ void link(double th, double &s, double &c) { sincos(th, &s, &c); }
+    static __device__ __forceinline__ void link(double th, double &s, double &c) { link_sincos(th, s, c); }
 };
 
 template <int BY_, class R = float>
