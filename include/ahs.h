@@ -21,8 +21,9 @@
  *  - Calls that move data or produce observables (init, step, measure, fields,
  *    set_fields, windings, records) synchronise the handle's stream before they
  *    return.  A handle is not thread-safe; distinct handles are independent.
- *  - Field storage is float32, structure of arrays: one plane of N^3 values per
- *    real component, site index x + N*(y + N*z) (x fastest).
+ *  - Field storage is float32 (FP64 in the FP64 precision mode), structure of
+ *    arrays: one plane of N^3 values per real component, site index
+ *    x + N*(y + N*z) (x fastest).
  */
 #ifndef AHS_H
 #define AHS_H
@@ -42,7 +43,7 @@ enum {
     AHS_ECUDA = -3,       /* a CUDA runtime call failed; message has the CUDA error */
     AHS_ESTATE = -4,      /* call not valid in the handle's state (e.g. not init)   */
     AHS_ENONFINITE = -5,  /* a measurement found a non-finite field value           */
-    AHS_ETIMEOUT = -6     /* a bounded device-side wait gave up                      */
+    AHS_ETIMEOUT = -6     /* reserved: no kernel of this library waits on another   */
 };
 
 /* ---- expansion eras: the value is p in a = (eta/eta0)^p (Eq. defm in
