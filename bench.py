@@ -461,7 +461,7 @@ def run_ours(args, N):
         "data": "synthetic", "config": workload(N, args.momenta_in_place),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                     "kernel": "step_tiled (plain leapfrog step)", "peak_kind": pk_kind,
+                     "kernel": "step_pair (plain leapfrog step, even N)", "peak_kind": pk_kind,
                      "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                      "launches": k_n, "measure_kernel_avg_ms": km_ms / max(km_n, 1),
                      "launch_shape": shape},

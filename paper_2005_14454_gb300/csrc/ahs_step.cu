@@ -24,6 +24,10 @@
 // orders every other shared array (each is written in B and read in C).
 // Tile coordinates wrap modulo N, so ragged tiles and N < 32 need no special path.
 // Site offsets are 32-bit (the handle limits N^3 below 2^32).
+// Kernels: step_tiled (any step, float32 and compensated, one site per thread),
+// step_pair (the plain float32 step on even N, two x-adjacent sites per thread on
+// 64-wide tiles, 8-byte field accesses), step_tiled64 (FP64 precision), and
+// batch_step (a persistent launch over the tiles of an ensemble).
 #include "ahs_device.cuh"
 
 #include <cstddef>
@@ -663,6 +667,273 @@ cudaError_t launch_variant64(const StepPtrs64 &p, const StepCoef64 &k, int N, in
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- paired plain step
+// The plain step (no measurement, float32) on 64 x BY tiles with two x-adjacent
+// sites per thread: each field of the pair is one 8-byte load or store, the link
+// phases of the pair go to shared memory as one 16-byte store per component, and
+// the per-plane bookkeeping serves two sites.  The arithmetic of each site is that
+// of tile_step, so the fields are bit-identical.  Needs an even N: a pair then
+// never straddles the periodic wrap and its offset is even (8-byte aligned).
+template <int BY_>
+struct Tile2 {
+    static constexpr int BX = 64, BY = BY_, NT = 32 * BY;
+    static constexpr int RX = BX + 2;                                // ring sites per row: x in [-1, BX]
+    static constexpr int RXP = BX + 4, RY = BY + 2, NR = RXP * RY;   // x in [-2, BX+1] (-2, BX+1: padding)
+    static constexpr int SXP = BX + 2, NS = SXP * (BY + 1);          // plaquettes: x in [-2, BX), y in [-1, BY)
+    static constexpr int NHA = 2 * RX + 2 * BY, NHB = BX + BY;
+    static_assert(NHA <= NT && NHB <= NT, "ring items must fit one pass of the CTA");
+    struct Plane {
+        float2 vx[NR], vy[NR], vz[NR], ph[NR];
+    };
+    struct Smem {
+        Plane pl[3];
+        float sxy[NS], sxz[NS], syz[NS];
+    };
+    // even for even ex: the pair (ex, ex+1) is one aligned float4 / float2
+    static __device__ __forceinline__ int r(int ex, int ey) { return (ey + 1) * RXP + (ex + 2); }
+    static __device__ __forceinline__ int q(int ex, int ey) { return (ey + 1) * SXP + (ex + 2); }
+};
+
+template <int BY>
+__global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCoef k, int N, int Dz)
+{
+    using T = Tile2<BY>;
+    using V2 = float2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
+    const ParamFields F{P};
+    const int tx = threadIdx.x, ty = threadIdx.y, t = tx + 32 * ty;
+    const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
+    const int zend = min(z0 + Dz, N);
+    const uint32_t NN = (uint32_t)N * (uint32_t)N;
+
+    // core pair: sites ex and ex+1 of row ty
+    const int ex = 2 * tx;
+    const int cx = wrapN(x0 + ex, N), cy = wrapN(y0 + ty, N);
+    const uint32_t coff = (uint32_t)cx + (uint32_t)N * (uint32_t)cy;
+    const bool valid = (x0 + ex < N) && (y0 + ty < N);
+    // ring items (single sites) of phases A and B
+    int hax = 0, hay = 0;
+    const bool hasA = t < T::NHA;
+    if (hasA) {
+        if (t < T::RX) { hax = t - 1; hay = -1; }
+        else if (t < 2 * T::RX) { hax = t - T::RX - 1; hay = BY; }
+        else if (t < 2 * T::RX + BY) { hax = -1; hay = t - 2 * T::RX; }
+        else { hax = T::BX; hay = t - 2 * T::RX - BY; }
+    }
+    const uint32_t haoff = (uint32_t)wrapN(x0 + hax, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hay, N);
+    const bool hasB = t < T::NHB;
+    const bool ringRow = t < T::BX;
+    const int hbx = ringRow ? t : -1, hby = ringRow ? -1 : t - T::BX;
+
+    auto ld2 = [&](const float *p, uint32_t o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
+    auto st2 = [&](float *p, uint32_t o, float a, float b) { *reinterpret_cast<float2 *>(p + o) = make_float2(a, b); };
+    struct Raw2 {
+        float2 tx, ty, tz, pr, pi;   // .x site ex, .y site ex+1
+    };
+    struct PE2 {
+        float2 qr, qi, ex, ey, ez;
+    };
+    auto load_raw2 = [&](uint32_t o) {
+        Raw2 a;
+        a.tx = ld2(P.tx, o); a.ty = ld2(P.ty, o); a.tz = ld2(P.tz, o);
+        a.pr = ld2(P.pr, o); a.pi = ld2(P.pim, o);
+        return a;
+    };
+    auto load_pe2 = [&](uint32_t o) {
+        PE2 a;
+        a.qr = ld2(P.qr, o); a.qi = ld2(P.qi, o);
+        a.ex = ld2(P.ex, o); a.ey = ld2(P.ey, o); a.ez = ld2(P.ez, o);
+        return a;
+    };
+    auto phaseA2 = [&](const Raw2 &a, typename T::Plane &pl) {
+        const int ri = T::r(ex, ty);
+        float s0, c0, s1, c1;
+        link_sincos(a.tx.x, s0, c0);
+        link_sincos(a.tx.y, s1, c1);
+        *reinterpret_cast<float4 *>(&pl.vx[ri]) = make_float4(c0, s0, c1, s1);
+        link_sincos(a.ty.x, s0, c0);
+        link_sincos(a.ty.y, s1, c1);
+        *reinterpret_cast<float4 *>(&pl.vy[ri]) = make_float4(c0, s0, c1, s1);
+        link_sincos(a.tz.x, s0, c0);
+        link_sincos(a.tz.y, s1, c1);
+        *reinterpret_cast<float4 *>(&pl.vz[ri]) = make_float4(c0, s0, c1, s1);
+        *reinterpret_cast<float4 *>(&pl.ph[ri]) = make_float4(a.pr.x, a.pi.x, a.pr.y, a.pi.y);
+    };
+    auto phaseA1 = [&](const Raw<float> &a, typename T::Plane &pl) {
+        const int ri = T::r(hax, hay);
+        float s, c;
+        link_sincos(a.tx, s, c);
+        pl.vx[ri] = make_float2(c, s);
+        link_sincos(a.ty, s, c);
+        pl.vy[ri] = make_float2(c, s);
+        link_sincos(a.tz, s, c);
+        pl.vz[ri] = make_float2(c, s);
+        pl.ph[ri] = make_float2(a.pr, a.pi);
+    };
+
+    int zc = wrapN(z0 - 1, N);
+    int z1 = next_plane(zc, N);
+    int z2 = next_plane(z1, N);
+
+    Raw2 rc = load_raw2((uint32_t)zc * NN + coff);
+    Raw<float> rh = hasA ? load_raw(F, (uint32_t)zc * NN + haoff) : Raw<float>{};
+    phaseA2(rc, S.pl[0]);
+    if (hasA) phaseA1(rh, S.pl[0]);
+    float2 thx = rc.tx, thy = rc.ty, thz = rc.tz;   // own theta pair of plane zz
+    rc = load_raw2((uint32_t)z1 * NN + coff);
+    if (hasA) rh = load_raw(F, (uint32_t)z1 * NN + haoff);
+    PE2 pe_next{}, pe_cur{};
+
+    // carried from plane zz-1 (own columns), per site of the pair
+    V2 phPrev[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    V2 vzPrev[2] = {make_float2(1.f, 0.f), make_float2(1.f, 0.f)};
+    float sxzPrev[2] = {0.f, 0.f}, syzPrev[2] = {0.f, 0.f};
+
+    int b = 0;
+    for (int zz = z0 - 1; zz < zend; ++zz) {
+        const int bn = b == 2 ? 0 : b + 1;
+        typename T::Plane &pc = S.pl[b];
+        typename T::Plane &pn = S.pl[bn];
+        const uint32_t oc = (uint32_t)zc * NN, o1 = (uint32_t)z1 * NN, o2 = (uint32_t)z2 * NN;
+        // ---- A: link phases and phi of plane zz+1
+        phaseA2(rc, pn);
+        if (hasA) phaseA1(rh, pn);
+        const float2 nthx = rc.tx, nthy = rc.ty, nthz = rc.tz;
+        if (zz + 2 <= zend) {
+            rc = load_raw2(o2 + coff);
+            if (hasA) rh = load_raw(F, o2 + haoff);
+        }
+        pe_cur = pe_next;
+        if (zz + 1 < zend) pe_next = load_pe2(o1 + coff);
+        __syncthreads();
+
+        // ---- B: plaquettes of plane zz (the pair + backward ring)
+        V2 Qxy[2], Qxz[2], Qyz[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int r0 = T::r(ex + j, ty), rxp = r0 + 1, ryp = r0 + T::RXP;
+            const V2 vx0 = pc.vx[r0], vy0 = pc.vy[r0], vz0 = pc.vz[r0];
+            Qxy[j] = plaquette(vx0, vy0, pc.vy[rxp], pc.vx[ryp]);
+            Qxz[j] = plaquette(vx0, vz0, pc.vz[rxp], pn.vx[r0]);
+            Qyz[j] = plaquette(vy0, vz0, pc.vz[ryp], pn.vy[r0]);
+        }
+        {
+            const int qi0 = T::q(ex, ty);
+            *reinterpret_cast<float2 *>(&S.sxy[qi0]) = make_float2(Qxy[0].y, Qxy[1].y);
+            *reinterpret_cast<float2 *>(&S.sxz[qi0]) = make_float2(Qxz[0].y, Qxz[1].y);
+            *reinterpret_cast<float2 *>(&S.syz[qi0]) = make_float2(Qyz[0].y, Qyz[1].y);
+        }
+        if (hasB) {
+            const int rb = T::r(hbx, hby), rbx = T::r(hbx + 1, hby), rby = T::r(hbx, hby + 1);
+            const V2 bx = pc.vx[rb], by = pc.vy[rb], bz = pc.vz[rb];
+            const int qh = T::q(hbx, hby);
+            S.sxy[qh] = plaquette(bx, by, pc.vy[rbx], pc.vx[rby]).y;
+            if (ringRow) S.syz[qh] = plaquette(by, bz, pc.vz[rby], pn.vy[rb]).y;
+            else S.sxz[qh] = plaquette(bx, bz, pc.vz[rbx], pn.vx[rb]).y;
+        }
+        __syncthreads();
+
+        // ---- C: kick and drift of plane zz, both sites
+        V2 p0s[2], vz0s[2];
+        if (zz >= z0 && valid) {
+            float qn[2][2], en[2][3];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int r0 = T::r(ex + j, ty), rxp = r0 + 1, ryp = r0 + T::RXP;
+                const int rxm = r0 - 1, rym = r0 - T::RXP;
+                const V2 p0 = pc.ph[r0], vx0 = pc.vx[r0], vy0 = pc.vy[r0], vz0 = pc.vz[r0];
+                const float qr = j ? pe_cur.qr.y : pe_cur.qr.x, qi = j ? pe_cur.qi.y : pe_cur.qi.x;
+                const float e0x = j ? pe_cur.ex.y : pe_cur.ex.x, e0y = j ? pe_cur.ey.y : pe_cur.ey.x;
+                const float e0z = j ? pe_cur.ez.y : pe_cur.ez.x;
+                const V2 hx = cmulc(pc.ph[rxp], vx0);
+                const V2 hy = cmulc(pc.ph[ryp], vy0);
+                const V2 hz = cmulc(pn.ph[r0], vz0);
+                const V2 bxh = cmul(pc.vx[rxm], pc.ph[rxm]);
+                const V2 byh = cmul(pc.vy[rym], pc.ph[rym]);
+                const V2 bzh = cmul(vzPrev[j], phPrev[j]);
+                const float hsr = ((hx.x + bxh.x) + (hy.x + byh.x)) + (hz.x + bzh.x);
+                const float hsi = ((hx.y + bxh.y) + (hy.y + byh.y)) + (hz.y + bzh.y);
+                const float mod2 = p0.x * p0.x + p0.y * p0.y;
+                const float potf = k.kpi_pot * (mod2 - k.sigma2);
+                qn[j][0] = k.cpi * qr + k.kpi_lap * (hsr - float(6) * p0.x) - potf * p0.x;
+                qn[j][1] = k.cpi * qi + k.kpi_lap * (hsi - float(6) * p0.y) - potf * p0.y;
+                const float jx = p0.x * hx.y - p0.y * hx.x;
+                const float jy = p0.x * hy.y - p0.y * hy.x;
+                const float jz = p0.x * hz.y - p0.y * hz.x;
+                const float sxy = Qxy[j].y, sxz = Qxz[j].y, syz = Qyz[j].y;
+                const float cxv = -(sxy - S.sxy[T::q(ex + j, ty - 1)]) - (sxz - sxzPrev[j]);
+                const float cyv = (sxy - S.sxy[T::q(ex + j - 1, ty)]) - (syz - syzPrev[j]);
+                const float czv = (sxz - S.sxz[T::q(ex + j - 1, ty)]) + (syz - S.syz[T::q(ex + j, ty - 1)]);
+                en[j][0] = k.ce * e0x + k.ke_curl * cxv + k.ke_cur * jx;
+                en[j][1] = k.ce * e0y + k.ke_curl * cyv + k.ke_cur * jy;
+                en[j][2] = k.ce * e0z + k.ke_curl * czv + k.ke_cur * jz;
+                p0s[j] = p0;
+                vz0s[j] = vz0;
+            }
+            const uint32_t o = oc + coff;
+            st2(P.qr1, o, qn[0][0], qn[1][0]);
+            st2(P.qi1, o, qn[0][1], qn[1][1]);
+            st2(P.ex1, o, en[0][0], en[1][0]);
+            st2(P.ey1, o, en[0][1], en[1][1]);
+            st2(P.ez1, o, en[0][2], en[1][2]);
+            st2(P.pr1, o, p0s[0].x + k.dphi * qn[0][0], p0s[1].x + k.dphi * qn[1][0]);
+            st2(P.pim1, o, p0s[0].y + k.dphi * qn[0][1], p0s[1].y + k.dphi * qn[1][1]);
+            float t1[2][3];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                t1[j][0] = (j ? thx.y : thx.x) + k.dtheta * en[j][0];
+                t1[j][1] = (j ? thy.y : thy.x) + k.dtheta * en[j][1];
+                t1[j][2] = (j ? thz.y : thz.x) + k.dtheta * en[j][2];
+                if (k.wrap) {
+                    t1[j][0] += kTwoPiF * floorf((kPiF - t1[j][0]) * kInvTwoPiF);
+                    t1[j][1] += kTwoPiF * floorf((kPiF - t1[j][1]) * kInvTwoPiF);
+                    t1[j][2] += kTwoPiF * floorf((kPiF - t1[j][2]) * kInvTwoPiF);
+                }
+            }
+            st2(P.tx1, o, t1[0][0], t1[1][0]);
+            st2(P.ty1, o, t1[0][1], t1[1][1]);
+            st2(P.tz1, o, t1[0][2], t1[1][2]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int r0 = T::r(ex + j, ty);
+                p0s[j] = pc.ph[r0];
+                vz0s[j] = pc.vz[r0];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            phPrev[j] = p0s[j];
+            vzPrev[j] = vz0s[j];
+            sxzPrev[j] = Qxz[j].y;
+            syzPrev[j] = Qyz[j].y;
+        }
+        thx = nthx; thy = nthy; thz = nthz;
+        zc = z1; z1 = z2; z2 = next_plane(z2, N);
+        b = bn;
+    }
+}
+
+template <int BY>
+cudaError_t launch_pair(const StepPtrs &p, const StepCoef &k, int N, int Dz, cudaStream_t st)
+{
+    using T = Tile2<BY>;
+    const size_t bytes = sizeof(typename T::Smem);
+    static int configured_device = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (configured_device != dev) {
+        e = cudaFuncSetAttribute(step_pair<BY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        configured_device = dev;
+    }
+    dim3 grid((N + T::BX - 1) / T::BX, (N + BY - 1) / BY, (N + Dz - 1) / Dz);
+    step_pair<BY><<<grid, dim3(32, BY), bytes, st>>>(p, k, N, Dz);
+    return cudaGetLastError();
+}
+
 template <int BY, bool C>
 cudaError_t launch_by(const StepPtrs &p, const StepCoef &k, int N, int Dz, bool measure, bool store,
                       double *partials, cudaStream_t st)
@@ -710,6 +981,7 @@ cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepS
         if (sh.by == 16) return launch_by<16, true>(p, k, N, sh.dz, measure, store, partials, st);
         return launch_by<8, true>(p, k, N, sh.dz, measure, store, partials, st);
     }
+    if (!measure && store && N % 2 == 0 && sh.by == 8) return launch_pair<8>(p, k, N, sh.dz, st);
     if (sh.by == 16) return launch_by<16, false>(p, k, N, sh.dz, measure, store, partials, st);
     return launch_by<8, false>(p, k, N, sh.dz, measure, store, partials, st);
 }
