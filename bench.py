@@ -476,7 +476,7 @@ def run_ours(args, N):
         line["ensemble"] = run_ensemble(torch)
     if not args.no_capacity and ws == 1 and not args.momenta_in_place:
         line["capacity"] = run_capacity(torch)
-    if not args.no_cpu:
+    if not args.no_cpu and ws == 1:       # the CPU baseline belongs to the one-GPU line
         line["cpu_baseline"] = cpu_baseline()
         line["cpu_baseline"]["one_core"] = cpu_baseline_one_core()
     group.close()
