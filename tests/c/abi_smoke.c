@@ -45,5 +45,22 @@ int main(void)
     free(F);
     printf("xi_w %.6f xi_l %.6f e_total %.6f\n", now.xi_w, now.xi_l, now.e_total);
     ahs_destroy(h);
+
+    /* a batch of two members of different size and era, run to their ends */
+    const int bn[2] = {16, 12}, bera[2] = {AHS_RADIATION, AHS_MATTER};
+    const uint64_t bseed[2] = {7, 8};
+    const int64_t bend[2] = {20, 13};
+    ahs_batch_t *b = ahs_batch_create(2, bn, bera, bseed, bend, 0.5, 0.1, 2.0, 1.0, 1.0, 0.0);
+    CHECK(b != NULL, "batch create");
+    CHECK(ahs_batch_init(b) == AHS_OK, "batch init");
+    CHECK(ahs_batch_run(b, 1000) == 20, "batch runs to the last member's end");
+    int64_t bnow = 0, bstop = 0;
+    CHECK(ahs_batch_step_info(b, 1, &bnow, &bstop) == AHS_OK && bnow == 13 && bstop == 13, "member stops at its end");
+    ahs_obs_t brec[4];
+    CHECK(ahs_batch_records(b, 0, brec, 4) == 2 && brec[1].step == 10, "member records");
+    ahs_obs_t bm;
+    CHECK(ahs_batch_measure(b, 1, &bm) == AHS_OK && bm.step == 13 && bm.nonfinite == 0, "member measure");
+    CHECK(ahs_batch_records(b, 5, brec, 4) == AHS_EINVAL, "bad member refused");
+    ahs_batch_destroy(b);
     return 0;
 }

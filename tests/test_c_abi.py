@@ -1,7 +1,7 @@
 """The boundary from C: tests/c/abi_smoke.c is compiled as C11 against
 include/ahs.h and linked to the engine library (both checked without a GPU); on
 a GPU it runs a small lattice through create, init, step, records, measure and
-fields, and the error paths."""
+fields, a two-member batch, and the error paths."""
 import os
 import subprocess
 
@@ -31,5 +31,5 @@ def test_header_compiles_as_c_and_links(program):
 def test_c_program_runs_a_lattice(program):
     out = subprocess.run([program], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stdout + out.stderr
-    assert out.stdout.count("ok ") == 13
+    assert out.stdout.count("ok ") == 20
     assert "xi_w" in out.stdout
