@@ -131,3 +131,27 @@ def test_1536_cubed_sampled_sites(eng, orc):
         ref = B.copy()
         orc.run(p, 3, 1, ref)
         assert np.allclose(A, ref[:, 2, 2, 2], rtol=2e-6, atol=2e-6), (A, ref[:, 2, 2, 2])
+
+
+def test_largest_lattice_1600_cubed(eng, orc):
+    """N = 1600, the largest side the 32-bit site offsets allow (N^3 < 2^32), with
+    in-place momenta (246 GB): one step from the random-phase start checked at
+    sampled sites against the oracle, corner sites included."""
+    import torch
+    from paper_2005_14454_gb300 import AHS_FIELD_ALL
+    N = 1600
+    free, _ = torch.cuda.mem_get_info()
+    if free < 60 * N ** 3 + (4 << 30):
+        pytest.skip(f"needs {60 * N ** 3 / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
+    sites = [(0, 0, 0), (N - 1, N - 1, N - 1), (N - 1, 0, N - 1), (0, N - 1, 800), (1234, 567, 1599)]
+    with eng.Lattice(N, measure_every=0, momenta_in_place=True, **PARAMS) as lat:
+        lat.init(3)
+        lat.step(2)
+        before = [lat.box(AHS_FIELD_ALL, x - 2, y - 2, z - 2, 5, 5, 5).astype(np.float64) for (x, y, z) in sites]
+        lat.step(1)
+        after = [lat.box(AHS_FIELD_ALL, x, y, z, 1, 1, 1).astype(np.float64)[:, 0, 0, 0] for (x, y, z) in sites]
+    p = orc.Params(N=5, era=1, **PARAMS)
+    for B, A in zip(before, after):
+        ref = B.copy()
+        orc.run(p, 2, 1, ref)
+        assert np.allclose(A, ref[:, 2, 2, 2], rtol=2e-6, atol=2e-6), (A, ref[:, 2, 2, 2])
