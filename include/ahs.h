@@ -141,10 +141,13 @@ typedef struct ahs_obs {
  * dt, couplings lambda0 and e0 (Eqs. 7-8), vacuum expectation value sigma, width
  * exponent s (lambda = lambda0 a^{-2(1-s)}, e = e0 a^{-(1-s)}, so the potential
  * and the current carry a^{2s}; Eq. 6 read with Eqs. 7-8), and era p in
- * {0, 1, 2}.  Allocates 80 bytes of device memory per site: all ten field
- * components double buffered, so a step reads one copy and writes the other.
- * Fields are undefined until ahs_init or
- * ahs_set_fields.  NULL on error (EINVAL, ENOMEM, ECUDA). */
+ * {0, 1, 2}.  The field storage -- 80 bytes of device memory per site by
+ * default: all ten field components double buffered, so a step reads one copy
+ * and writes the other (see AHS_OPT_PRECISION and AHS_OPT_MOMENTA_IN_PLACE for
+ * the other layouts) -- is allocated by the first ahs_init or ahs_set_fields,
+ * which return AHS_ENOMEM if it does not fit; options that change the layout
+ * free it.  Fields are undefined until ahs_init or ahs_set_fields.  NULL on
+ * error (EINVAL, ENOMEM, ECUDA). */
 ahs_t *ahs_create(int N, double dx, double dt, double lambda0, double e0,
                   double sigma, double s, int era);
 
@@ -209,7 +212,9 @@ int ahs_set_stream(ahs_t *h, void *cuda_stream);
 enum { AHS_KERNEL_STEP = 0, AHS_KERNEL_STEP_MEASURE = 1 };
 int ahs_kernel_time(ahs_t *h, int kind, double *ms_total, int64_t *launches, int reset);
 
-/* ahs_device_bytes -- device memory held by the handle. */
+/* ahs_device_bytes -- device memory of the handle: its field storage (allocated
+ * or, before the first ahs_init / ahs_set_fields, to be allocated), measurement
+ * partials and records. */
 int ahs_device_bytes(ahs_t *h, size_t *bytes);
 
 /* ---- batched ensembles ---------------------------------------------------

@@ -151,14 +151,23 @@ cudaError_t launch_current(const ahs_t *h, bool measure, bool store)
                        h->partials, h->stream, h->precision == AHS_PREC_FP32_COMPENSATED);
 }
 
-// (re)allocate the field storage for the handle's precision
-int alloc_fields(ahs_t *h)
+// the storage layout of the handle's precision and storage mode; frees any field
+// storage (the fields are then undefined until ahs_init or ahs_set_fields)
+void reset_fields(ahs_t *h)
 {
     if (h->base) cudaFree(h->base);
     h->base = nullptr;
     h->ready = false;
+    h->cur = 0;
     h->planes = h->precision == AHS_PREC_FP32_COMPENSATED ? kFields + kLowPlanes : kFields;
     h->esize = h->precision == AHS_PREC_FP64 ? sizeof(double) : sizeof(float);
+}
+
+// allocate the field storage on first use (ahs_init, ahs_set_fields), so that the
+// precision and storage options are set before the bytes are committed
+int alloc_fields(ahs_t *h)
+{
+    if (h->base) return AHS_OK;
     const size_t bytes = h->field_bytes();
     cudaError_t e = cudaMalloc(&h->base, bytes);
     if (e != cudaSuccess) {
@@ -279,22 +288,17 @@ ahs_t *ahs_create(int N, double dx, double dt, double lambda0, double e0, double
         delete h;
         return nullptr;
     }
-    if (alloc_fields(h) != AHS_OK) {
-        delete h;
-        return nullptr;
-    }
+    reset_fields(h);
     h->nblocks = step_shape(N, 0, 0).blocks;
     cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * NQ * (size_t)h->nblocks);
     if (e != cudaSuccess) {
         fail(AHS_ENOMEM, "cudaMalloc(partials): %s", cudaGetErrorString(e));
         cudaGetLastError();
-        cudaFree(h->base);
         delete h;
         return nullptr;
     }
     if (ensure_records(h, 64) != AHS_OK) {
         cudaFree(h->partials);
-        cudaFree(h->base);
         delete h;
         return nullptr;
     }
@@ -335,6 +339,7 @@ int ahs_init(ahs_t *h, uint64_t seed)
 {
     if (!h) return fail(AHS_EINVAL, "null handle");
     if (int r = set_device(h)) return r;
+    if (int r = alloc_fields(h)) return r;
     h->cur = 0;
     h->n = 0;
     if (h->precision == AHS_PREC_FP64) {
@@ -395,8 +400,7 @@ int ahs_set_option(ahs_t *h, int key, double v)
         if (h->stream) cudaStreamSynchronize(h->stream);
         else cudaDeviceSynchronize();
         h->precision = (int)v;
-        if (int r = alloc_fields(h)) return r;
-        h->cur = 0;
+        reset_fields(h);
         return ok();
     }
     case AHS_OPT_COOLING:
@@ -419,8 +423,7 @@ int ahs_set_option(ahs_t *h, int key, double v)
         if (h->stream) cudaStreamSynchronize(h->stream);
         else cudaDeviceSynchronize();
         h->inplace = (int)v;
-        if (int r = alloc_fields(h)) return r;
-        h->cur = 0;
+        reset_fields(h);
         return ok();
     }
     case AHS_OPT_N:
@@ -571,6 +574,7 @@ int ahs_set_fields(ahs_t *h, int which, const void *src, size_t bytes)
     const size_t pb = h->esize * h->V;
     if (bytes != pb * count) return fail(AHS_EINVAL, "buffer is %zu bytes, field needs %zu", bytes, pb * count);
     if (int r = set_device(h)) return r;
+    if (int r = alloc_fields(h)) return r;
     if (!h->ready) {
         // a partial set on a fresh handle leaves the other fields zero
         for (int f = 0; f < h->planes; ++f)
