@@ -102,10 +102,10 @@ enum {
  * reads at neighbours, stay double-buffered.  Device storage drops from 80 to 60
  * bytes per site (a 1536^3 lattice takes 217 GB).  The fields, records and the
  * results of every call are bit-identical to the default storage.  Costs: a
- * measuring step runs as two launches (the measurement, then the step), because
- * its Gauss residual reads the old E of neighbouring sites that the fused step
- * would overwrite; ahs_autotune returns AHS_ESTATE (it times real steps, which
- * would advance the momenta). */
+ * measuring step runs as two launches (the Gauss residual first, since it reads
+ * the old E of neighbouring sites that the fused step overwrites, then the step
+ * with the rest of the measurement); ahs_autotune returns AHS_ESTATE (it times
+ * real steps, which would advance the momenta). */
 
 typedef struct ahs ahs_t;
 

@@ -141,14 +141,17 @@ int launch_blocks(const ahs_t *h)
     return step_shape(h->N, h->tile_y, h->zchunk).blocks;
 }
 
-// one step launch (measure: diagnostics into the partials; store: write n+1)
-cudaError_t launch_current(const ahs_t *h, bool measure, bool store)
+// one step launch (measure: diagnostics into the partials; store: write n+1;
+// gauss false: the Gauss residual's slots were written by launch_gauss)
+cudaError_t launch_current(const ahs_t *h, bool measure, bool store, bool gauss = true)
 {
     if (h->precision == AHS_PREC_FP64)
         return launch_step64(pointers64(h), coefficients64(h, h->n), h->N, step_shape(h->N, 8, h->zchunk), measure,
                              store, h->partials, h->stream);
-    return launch_step(pointers(h), coefficients(h, h->n), h->N, step_shape(h->N, h->tile_y, h->zchunk), measure, store,
-                       h->partials, h->stream, h->precision == AHS_PREC_FP32_COMPENSATED);
+    StepCoef k = coefficients(h, h->n);
+    k.gauss = gauss ? 1 : 0;
+    return launch_step(pointers(h), k, h->N, step_shape(h->N, h->tile_y, h->zchunk), measure, store, h->partials,
+                       h->stream, h->precision == AHS_PREC_FP32_COMPENSATED);
 }
 
 // the storage layout of the handle's precision and storage mode; frees any field
@@ -485,9 +488,10 @@ int ahs_step(ahs_t *h, int nsteps)
         const int nb = launch_blocks(h);
         if (meas && h->inplace) {
             // the Gauss residual reads neighbours' old E, which an in-place step
-            // overwrites: measure first, then step
-            CU(launch_current(h, true, false));
-            CU(launch_current(h, false, true));
+            // overwrites: it goes first, into the measuring launch's partial rows
+            CU(launch_gauss(pointers(h), coefficients(h, h->n), h->N, step_shape(h->N, h->tile_y, h->zchunk),
+                            h->partials, h->stream));
+            CU(launch_current(h, true, true, false));
         } else {
             CU(launch_current(h, meas, true));
         }

@@ -195,6 +195,33 @@ static __device__ __forceinline__ size_t sidx(int x, int y, int z, int N)
     return (size_t)x + (size_t)N * ((size_t)y + (size_t)N * (size_t)z);
 }
 
+// ---------------------------------------------------------------- explicit roundings
+// Arithmetic that the compiler may not contract into fused multiply-adds of its own
+// choosing: the diagnostics of a measuring step are evaluated with these, so that
+// every kernel that measures -- the fused measuring step, its batched form, the
+// separate Gauss launch -- gives the same bits whatever the surrounding code.
+static __device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+static __device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+static __device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+static __device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+static __device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+static __device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+static __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+static __device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---------------------------------------------------------------- Gauss residual
+// G(x) = sum_i (E_i(x) - E_i(x-i)) / dx - m_gauss Im(conj(phi) Pi) of one site (the
+// stored momenta at n - 1/2 with phi^n), every rounding explicit.
+template <class R>
+static __device__ __forceinline__ R gauss_site(R ex, R exm, R ey, R eym, R ez, R ezm, R inv_dx, R m_gauss, R pr,
+                                               R pim, R qr, R qi)
+{
+    const R div = rn_mul(rn_add(rn_add(rn_sub(ex, exm), rn_sub(ey, eym)), rn_sub(ez, ezm)), inv_dx);
+    return rn_sub(div, rn_mul(m_gauss, rn_sub(rn_mul(pr, qi), rn_mul(pim, qr))));
+}
+template <class R>
+static __device__ __forceinline__ R square_add(R g, R acc) { return rn_fma(g, g, acc); }
+
 // ---------------------------------------------------------------- reduction
 // per-thread sums of one tile: float32 (FP64 for the FP64 mode) along the z-march
 template <class R>
@@ -217,8 +244,11 @@ static __device__ __forceinline__ void acc_zero(AccT<R> &a)
 
 // Block reduction of the sums to one row of FP64 partials: in the sums' type within
 // a warp, FP64 across warps in a fixed order (deterministic for a launch shape).
+// which slots of the partial row a block writes
+enum { ROW_ALL = 0, ROW_NO_GAUSS = 1, ROW_GAUSS_ONLY = 2 };
+
 template <int NT, class R>
-static __device__ void block_reduce_store(AccT<R> &a, double *out)
+static __device__ void block_reduce_store(AccT<R> &a, double *out, int slots = ROW_ALL)
 {
     constexpr int NW = NT / 32;
     __shared__ double red[NW][NQ];
@@ -243,7 +273,8 @@ static __device__ void block_reduce_store(AccT<R> &a, double *out)
     }
     __syncthreads();
     const int t = threadIdx.x + blockDim.x * threadIdx.y;
-    if (t < NQ) {
+    const bool gauss_slot = t == Q_G2 || t == Q_GMAX;
+    if (t < NQ && (slots == ROW_ALL || (slots == ROW_NO_GAUSS) != gauss_slot)) {
         double v = red[0][t];
         for (int w = 1; w < NW; ++w) v = (t == Q_GMAX) ? fmax(v, red[w][t]) : v + red[w][t];
         out[t] = v;

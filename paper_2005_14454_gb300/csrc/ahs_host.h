@@ -77,6 +77,7 @@ inline StepCoef coefficients(const LatticeParams *h, int64_t n)
     const double kappa = P.c * (1.0 + P.delta) / (1.0 + P.omega);
     k.m_gauss = (float)(2.0 * h->e0 * h->e0 * kappa);
     k.inv_dx = (float)(1.0 / dx);
+    k.gauss = 1;
     return k;
 }
 
@@ -102,6 +103,7 @@ inline StepCoef64 coefficients64(const LatticeParams *h, int64_t n)
     const Scalars P = scalars(h, n - 1);
     k.m_gauss = 2.0 * h->e0 * h->e0 * P.c * (1.0 + P.delta) / (1.0 + P.omega);
     k.inv_dx = 1.0 / dx;
+    k.gauss = 1;
     return k;
 }
 

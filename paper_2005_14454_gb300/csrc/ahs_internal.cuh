@@ -61,6 +61,8 @@ struct StepCoef {
     float m_mag;    // 1/(e0^2 c dx^4)
     float m_gauss;  // 2 e0^2 kappa_{n-1}
     float inv_dx;
+    int gauss;      // 1: a measuring step computes the Gauss residual itself; 0: an
+                    // earlier launch (launch_gauss) wrote it into the partial rows
 };
 
 // the coefficients of StepCoef without rounding, for the FP64 mode
@@ -70,6 +72,7 @@ struct StepCoef64 {
     double dphi, dtheta;
     int wrap;
     double m_grad, m_pot, m_el, m_mag, m_gauss, inv_dx;
+    int gauss;
 };
 
 // Scalars the final reduction needs to turn sums into an observable record.
@@ -89,6 +92,11 @@ StepShape step_shape(int N, int tile_y, int zchunk);   // tile_y/zchunk 0: autom
 cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, bool measure, bool store,
                         double *partials, cudaStream_t st, bool compensated = false);
 // FP64 precision: the tiled step in double, 8-row tiles (sh.by must be 8)
+// The Gauss residual alone (the Q_G2 and Q_GMAX slots of the partial rows of the
+// measuring launch of the same shape, in the same order of operations), for
+// measuring steps whose launch overwrites E in place.
+cudaError_t launch_gauss(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, double *partials,
+                         cudaStream_t st);
 cudaError_t launch_step64(const StepPtrs64 &p, const StepCoef64 &k, int N, const StepShape &sh, bool measure,
                           bool store, double *partials, cudaStream_t st);
 cudaError_t launch_init_fp64(double *pr, double *pim, int N, uint64_t seed, double sigma, cudaStream_t st);

@@ -226,11 +226,16 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b)
     return make_double2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
-// Q = V_i(x) conj(V_j(x)) * V_j(x+i) conj(V_i(x+j))
+// Q = V_i(x) conj(V_j(x)) * V_j(x+i) conj(V_i(x+j)); the last product's roundings are
+// explicit, since its real part (cos of the plaquette) is a diagnostic only
 template <class V2>
 __device__ __forceinline__ V2 plaquette(V2 vi, V2 vj, V2 vjp, V2 vip)
 {
-    return cmul(cmulc(vi, vj), cmulc(vjp, vip));
+    const V2 a = cmulc(vi, vj), b = cmulc(vjp, vip);
+    V2 q;
+    q.x = rn_fma(a.x, b.x, -rn_mul(a.y, b.y));
+    q.y = rn_fma(a.x, b.y, rn_mul(a.y, b.x));
+    return q;
 }
 
 __device__ __forceinline__ int next_plane(int z, int N) { return z + 1 == N ? 0 : z + 1; }
@@ -302,7 +307,9 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
     if (hasA) rh = load_raw(P, (uint32_t)z1 * NN + haoff);
     PE<R> pe_next{}, pe_cur{};
     R ezPrev = 0;
-    if (MEASURE) ezPrev = P.in(FEZ, (uint32_t)zc * NN + coff);
+    // the Gauss residual of a measuring step, unless an earlier launch wrote it
+    const bool gauss = MEASURE && k.gauss != 0;
+    if (gauss) ezPrev = P.in(FEZ, (uint32_t)zc * NN + coff);
     // old E of this thread's backward-ring site (Gauss residual), loaded one plane ahead
     R eRing = 0, eRingNext = 0;
 
@@ -332,7 +339,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         if (zz + 1 < zend) pe_next = load_pe<COMP>(P, o1 + coff);
         if (MEASURE) {
             eRing = eRingNext;
-            if (hasB && zz + 1 < zend) eRingNext = P.in(ringRow ? FEY : FEX, o1 + hboff);
+            if (gauss && hasB && zz + 1 < zend) eRingNext = P.in(ringRow ? FEY : FEX, o1 + hboff);
         }
         __syncthreads();
 
@@ -365,8 +372,10 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
             S.yy[wi] = YyCar;
             const R tz0 = thz;
             S.yz[wi] = link_phase_v(p0.x, p0.y, pz.x, pz.y, vz0.x, vz0.y, [&] { return tz0; });
-            S.ex[T::q(tx, ty)] = pe_cur.ex;
-            S.ey[T::q(tx, ty)] = pe_cur.ey;
+            if (gauss) {
+                S.ex[T::q(tx, ty)] = pe_cur.ex;
+                S.ey[T::q(tx, ty)] = pe_cur.ey;
+            }
             if (hasB) {
                 const int rh0 = T::r(hyx, hyy), wh = T::w(hyx, hyy);
                 const uint32_t ho = oc + hyoff;
@@ -380,8 +389,10 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
                 }
                 const V2 q = pn.ph[rh0], v = pc.vz[rh0];
                 S.yz[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTZ, ho); });
-                if (ringRow) S.ey[T::q(hbx, hby)] = eRing;
-                else S.ex[T::q(hbx, hby)] = eRing;
+                if (gauss) {
+                    if (ringRow) S.ey[T::q(hbx, hby)] = eRing;
+                    else S.ex[T::q(hbx, hby)] = eRing;
+                }
             }
         }
         __syncthreads();
@@ -441,29 +452,44 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
             }
 
             if (MEASURE) {
-                const R half = R(0.5), third = R(1) / R(3);
-                const R pbr = COMP ? half * ((pe_cur.qr + qnr) + (pe_cur.qrl + qnrl)) : half * (pe_cur.qr + qnr);
-                const R pbi = COMP ? half * ((pe_cur.qi + qni) + (pe_cur.qil + qnil)) : half * (pe_cur.qi + qni);
-                const R K = pbr * pbr + pbi * pbi;
-                const R gxr = hx.x - p0.x, gxi = hx.y - p0.y, gyr = hy.x - p0.x, gyi = hy.y - p0.y;
-                const R gzr = hz.x - p0.x, gzi = hz.y - p0.y;
-                const R G = k.m_grad * ((gxr * gxr + gxi * gxi) + (gyr * gyr + gyi * gyi) + (gzr * gzr + gzi * gzi));
-                const R dm = mod2 - k.sigma2;
-                const R V = k.m_pot * dm * dm;
-                const R ebx = COMP ? half * ((pe_cur.ex + enx) + (pe_cur.exl + enxl)) : half * (pe_cur.ex + enx);
-                const R eby = COMP ? half * ((pe_cur.ey + eny) + (pe_cur.eyl + enyl)) : half * (pe_cur.ey + eny);
-                const R ebz = COMP ? half * ((pe_cur.ez + enz) + (pe_cur.ezl + enzl)) : half * (pe_cur.ez + enz);
-                const R El = k.m_el * (ebx * ebx + eby * eby + ebz * ebz);
-                const R B = k.m_mag * ((R(1) - Qxy.x) + (R(1) - Qxz.x) + (R(1) - Qyz.x));
-                const R L = K - G - V + El - B;
-                const R rho = K + G + V + El + B;
-                const R pres = K - G * third - V + (El + B) * third;
-                const R div = ((pe_cur.ex - S.ex[T::q(tx - 1, ty)]) + (pe_cur.ey - S.ey[T::q(tx, ty - 1)]) +
-                               (pe_cur.ez - ezPrev)) * k.inv_dx;
-                const R g = div - k.m_gauss * (p0.x * pe_cur.qi - p0.y * pe_cur.qr);
-                acc.s[Q_K] += K; acc.s[Q_G] += G; acc.s[Q_V] += V; acc.s[Q_EL] += El; acc.s[Q_B] += B;
-                acc.s[Q_L] += L; acc.s[Q_KL] += K * L; acc.s[Q_GL] += G * L; acc.s[Q_PL] += pres * L;
-                acc.s[Q_RL] += rho * L; acc.s[Q_G2] += g * g;
+                // diagnostics (Eqs. diagxi, diagvel) with explicit roundings: the
+                // momenta at n are the means of those at n -+ 1/2
+                const R half = R(0.5), third = R(1) / R(3), one = R(1);
+                auto mean = [&](R a, R al, R b, R bl) {
+                    return COMP ? rn_mul(half, rn_add(rn_add(a, b), rn_add(al, bl))) : rn_mul(half, rn_add(a, b));
+                };
+                auto sq2 = [](R a, R b) { return rn_fma(a, a, rn_mul(b, b)); };
+                const R pbr = mean(pe_cur.qr, pe_cur.qrl, qnr, qnrl);
+                const R pbi = mean(pe_cur.qi, pe_cur.qil, qni, qnil);
+                const R K = sq2(pbr, pbi);
+                const R G = rn_mul(k.m_grad, rn_add(rn_add(sq2(rn_sub(hx.x, p0.x), rn_sub(hx.y, p0.y)),
+                                                           sq2(rn_sub(hy.x, p0.x), rn_sub(hy.y, p0.y))),
+                                                    sq2(rn_sub(hz.x, p0.x), rn_sub(hz.y, p0.y))));
+                const R dm = rn_sub(mod2, k.sigma2);
+                const R V = rn_mul(rn_mul(k.m_pot, dm), dm);
+                const R ebx = mean(pe_cur.ex, pe_cur.exl, enx, enxl);
+                const R eby = mean(pe_cur.ey, pe_cur.eyl, eny, enyl);
+                const R ebz = mean(pe_cur.ez, pe_cur.ezl, enz, enzl);
+                const R El = rn_mul(k.m_el, rn_fma(ebz, ebz, sq2(ebx, eby)));
+                const R B = rn_mul(k.m_mag, rn_add(rn_add(rn_sub(one, Qxy.x), rn_sub(one, Qxz.x)), rn_sub(one, Qyz.x)));
+                const R L = rn_sub(rn_add(rn_sub(rn_sub(K, G), V), El), B);
+                const R rho = rn_add(rn_add(rn_add(rn_add(K, G), V), El), B);
+                const R pres = rn_add(rn_sub(rn_sub(K, rn_mul(G, third)), V), rn_mul(rn_add(El, B), third));
+                const R g = gauss ? gauss_site(pe_cur.ex, S.ex[T::q(tx - 1, ty)], pe_cur.ey, S.ey[T::q(tx, ty - 1)],
+                                               pe_cur.ez, ezPrev, k.inv_dx, k.m_gauss, p0.x, p0.y, pe_cur.qr,
+                                               pe_cur.qi)
+                                  : R(0);
+                acc.s[Q_K] = rn_add(acc.s[Q_K], K);
+                acc.s[Q_G] = rn_add(acc.s[Q_G], G);
+                acc.s[Q_V] = rn_add(acc.s[Q_V], V);
+                acc.s[Q_EL] = rn_add(acc.s[Q_EL], El);
+                acc.s[Q_B] = rn_add(acc.s[Q_B], B);
+                acc.s[Q_L] = rn_add(acc.s[Q_L], L);
+                acc.s[Q_KL] = rn_fma(K, L, acc.s[Q_KL]);
+                acc.s[Q_GL] = rn_fma(G, L, acc.s[Q_GL]);
+                acc.s[Q_PL] = rn_fma(pres, L, acc.s[Q_PL]);
+                acc.s[Q_RL] = rn_fma(rho, L, acc.s[Q_RL]);
+                acc.s[Q_G2] = square_add(g, acc.s[Q_G2]);
                 acc.gmax = fmax(acc.gmax, fabs(g));
                 if (!isfinite(rho) || !isfinite(L) || !isfinite(g)) acc.nf += 1;
 
@@ -524,7 +550,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         vzPrev = vz0;
         sxzPrev = Qxz.y;
         syzPrev = Qyz.y;
-        if (MEASURE && zz >= z0) ezPrev = pe_cur.ez;
+        if (gauss && zz >= z0) ezPrev = pe_cur.ez;
         YxCar = YxNext;
         YyCar = YyNext;
         thx = nthx; thy = nthy; thz = nthz;
@@ -532,7 +558,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         b = bn;
     }
 
-    if (MEASURE) block_reduce_store<32 * BY>(acc, partial_row);
+    if (MEASURE) block_reduce_store<32 * BY>(acc, partial_row, gauss ? ROW_ALL : ROW_NO_GAUSS);
 }
 
 // Residency: a plain step fits 64 registers, so four 8-warp CTAs share an SM
@@ -934,6 +960,44 @@ cudaError_t launch_pair(const StepPtrs &p, const StepCoef &k, int N, int Dz, cud
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- Gauss residual alone
+// The Gauss residual of a measuring step (Eq. 5 in discrete form: the stored
+// momenta at n - 1/2 with phi^n) for a measuring launch that overwrites E in place:
+// the same tiles, z-chunks, per-thread order of accumulation and block reduction
+// as the measuring step, writing only the Q_G2 and Q_GMAX slots of its partial
+// rows, so the record equals the one the fused measurement gives.
+template <int BY>
+__global__ void __launch_bounds__(32 * BY) gauss_tiled(StepPtrs P, StepCoef k, int N, int Dz, double *partials)
+{
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
+    const int zend = min(z0 + Dz, N);
+    const uint32_t NN = (uint32_t)N * (uint32_t)N;
+    const int cx = wrapN(x0 + tx, N), cy = wrapN(y0 + ty, N);
+    const uint32_t coff = (uint32_t)cx + (uint32_t)N * (uint32_t)cy;
+    const uint32_t xmoff = (uint32_t)wrapN(cx - 1, N) + (uint32_t)N * (uint32_t)cy;
+    const uint32_t ymoff = (uint32_t)cx + (uint32_t)N * (uint32_t)wrapN(cy - 1, N);
+    const bool valid = (x0 + tx < N) && (y0 + ty < N);
+    AccT<float> acc;
+    acc_zero(acc);
+    float ezPrev = __ldg(P.ez + (uint32_t)wrapN(z0 - 1, N) * NN + coff);
+    for (int zz = z0; zz < zend; ++zz) {
+        const uint32_t o = (uint32_t)zz * NN;
+        const float ex = __ldg(P.ex + o + coff), ey = __ldg(P.ey + o + coff), ez = __ldg(P.ez + o + coff);
+        if (valid) {
+            const float exm = __ldg(P.ex + o + xmoff), eym = __ldg(P.ey + o + ymoff);
+            const float pr = __ldg(P.pr + o + coff), pim = __ldg(P.pim + o + coff);
+            const float qr = __ldg(P.qr + o + coff), qi = __ldg(P.qi + o + coff);
+            const float g = gauss_site(ex, exm, ey, eym, ez, ezPrev, k.inv_dx, k.m_gauss, pr, pim, qr, qi);
+            acc.s[Q_G2] = square_add(g, acc.s[Q_G2]);
+            acc.gmax = fmax(acc.gmax, fabs(g));
+        }
+        ezPrev = ez;
+    }
+    const size_t bi = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+    block_reduce_store<32 * BY>(acc, partials + bi * NQ, ROW_GAUSS_ONLY);
+}
+
 template <int BY, bool C>
 cudaError_t launch_by(const StepPtrs &p, const StepCoef &k, int N, int Dz, bool measure, bool store,
                       double *partials, cudaStream_t st)
@@ -994,6 +1058,15 @@ cudaError_t launch_step64(const StepPtrs64 &p, const StepCoef64 &k, int N, const
     if (measure) return launch_variant64<true, false>(p, k, N, sh.dz, partials, st);
     if (store) return launch_variant64<false, true>(p, k, N, sh.dz, partials, st);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gauss(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, double *partials,
+                         cudaStream_t st)
+{
+    dim3 grid((N + 31) / 32, (N + sh.by - 1) / sh.by, (N + sh.dz - 1) / sh.dz);
+    if (sh.by == 16) gauss_tiled<16><<<grid, dim3(32, 16), 0, st>>>(p, k, N, sh.dz, partials);
+    else gauss_tiled<8><<<grid, dim3(32, 8), 0, st>>>(p, k, N, sh.dz, partials);
+    return cudaGetLastError();
 }
 
 }  // namespace eng

@@ -135,7 +135,8 @@ def test_batch_core_growth_equals_single_runs(pkg):
                 lat.init(sd)
                 lat.step(ne)
                 assert np.array_equal(b.state(i), lat.state()), i
-                assert b.records(i) == lat.records()
+                for rb, rs in zip(b.records(i), lat.records()):
+                    assert rb == rs, {k: (rb[k], rs[k]) for k in rb if rb[k] != rs[k]}
 
 
 def test_ensemble_means_match_oracle(pkg, orc):
