@@ -658,7 +658,7 @@ int ahs_autotune(ahs_t *h)
     const bool comp = h->precision == AHS_PREC_FP32_COMPENSATED;
     cudaEvent_t e0 = event_at(h, 0), e1 = event_at(h, 1);
     if (!e0 || !e1) return fail(AHS_ECUDA, "cudaEventCreate failed");
-    const int bys[2] = {8, 16}, dzs[6] = {4, 8, 16, 32, 64, 128};
+    const int bys[2] = {8, 16}, dzs[8] = {0, 4, 8, 16, 32, 64, 128, 256};   // 0: the automatic chunk
     double best = 1e300;
     int best_by = 8, best_dz = 0;
     for (int by : bys)

@@ -1018,8 +1018,11 @@ StepShape step_shape(int N, int tile_y, int zchunk)
         s.dz = zchunk < N ? zchunk : N;
     } else {
         // several waves of CTAs on 152 SMs, marches long enough to amortise the two
-        // prologue planes of each chunk
-        s.dz = N >= 512 ? 64 : N >= 256 ? 32 : N >= 64 ? 16 : (N < 8 ? N : 8);
+        // prologue planes of each chunk; from 512^3 on, the chunk with the shortest
+        // period of nine plain steps and one measuring step among those timed at
+        // 512^3 (96), 768^3 (128), 1024^3 (192) and 1536^3 (128)
+        s.dz = N >= 1280 ? 128 : N >= 896 ? 192 : N >= 640 ? 128 : N >= 512 ? 96 : N >= 256 ? 32 : N >= 64 ? 16
+                                                                                       : (N < 8 ? N : 8);
     }
     s.blocks = ((N + 31) / 32) * ((N + s.by - 1) / s.by) * ((N + s.dz - 1) / s.dz);
     return s;
