@@ -18,6 +18,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -157,12 +158,21 @@ class ClockSampler:
 STEP_KERNEL_SOURCES = ("ahs_step.cu", "ahs_device.cuh", "ahs_internal.cuh")
 
 
+def code_only(text):
+    """C++/CUDA source without its comments and blank lines (edits to comments do not
+    change the compiled kernel)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+    return "\n".join(ln for ln in lines if ln)
+
+
 def kernel_hash():
-    """Hash of the sources the step kernel is compiled from."""
+    """Hash of the code (comments removed) of the sources the step kernel is
+    compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2005_14454_gb300", "csrc")
     for f in STEP_KERNEL_SOURCES:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(code_only(open(os.path.join(csrc, f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -26,8 +26,9 @@
 // Site offsets are 32-bit (the handle limits N^3 below 2^32).
 // Kernels: step_tiled (any step, float32 and compensated, one site per thread),
 // step_pair (the plain float32 step on even N, two x-adjacent sites per thread on
-// 64-wide tiles, 8-byte field accesses), step_tiled64 (FP64 precision), and
-// batch_step (a persistent launch over the tiles of an ensemble).
+// 64-wide tiles, 8-byte field accesses), step_tiled64 (FP64 precision), batch_step
+// (a persistent launch over the tiles of an ensemble), and gauss_tiled (the Gauss
+// residual alone, ahead of a measuring step that updates Pi and E in place).
 #include "ahs_device.cuh"
 
 #include <cstddef>

@@ -75,6 +75,7 @@ CASES = [
     (4, 1, 0.0), (5, 1, 0.0), (7, 2, 0.0),                  # smaller than one tile, odd N
     (8, 1, 0.0), (24, 1, 0.0), (40, 1, 0.0), (64, 1, 0.0),   # radiation, several tiles, ragged
     (24, 2, 0.0), (24, 0, 0.0), (36, 2, 1.0), (20, 1, 1.0),  # matter, Minkowski, s = 1
+    (6, 1, 0.0), (66, 2, 0.0), (65, 1, 0.0),                # paired step with a 2-site ragged tile; odd N > 64
 ]
 
 

@@ -48,3 +48,11 @@ def test_single_process_group_is_a_no_op(monkeypatch):
     assert g.ws == 1 and g.max(3.25) == 3.25
     g.barrier()
     g.close()
+
+
+def test_kernel_hash_ignores_comments_only():
+    import bench
+    src = "// head\nint f(int a) { /* two\nlines */ return a + 1; // tail\n}\n\n"
+    assert bench.code_only(src) == "int f(int a) {  return a + 1;\n}"
+    assert bench.code_only(src) == bench.code_only(src.replace("// tail", "// other words"))
+    assert bench.code_only(src) != bench.code_only(src.replace("a + 1", "a + 2"))
