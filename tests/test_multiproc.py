@@ -56,3 +56,12 @@ def test_kernel_hash_ignores_comments_only():
     assert bench.code_only(src) == "int f(int a) {  return a + 1;\n}"
     assert bench.code_only(src) == bench.code_only(src.replace("// tail", "// other words"))
     assert bench.code_only(src) != bench.code_only(src.replace("a + 1", "a + 2"))
+
+
+def test_failing_extra_leg_is_reported_not_raised():
+    import bench
+
+    def no_room(_):
+        raise MemoryError("217 GB do not fit")
+    assert bench.extra_leg(no_room, None) == {"unavailable": "MemoryError: 217 GB do not fit"}
+    assert bench.extra_leg(lambda x: {"value": x}, 3) == {"value": 3}
