@@ -496,8 +496,10 @@ def run_ours(args, N):
     if not args.no_capacity and ws == 1 and not args.momenta_in_place:
         line["capacity"] = extra_leg(run_capacity, torch)
     if not args.no_cpu and ws == 1:       # the CPU baseline belongs to the one-GPU line
-        line["cpu_baseline"] = cpu_baseline()
-        line["cpu_baseline"]["one_core"] = cpu_baseline_one_core()
+        cb = extra_leg(cpu_baseline)
+        if "unavailable" not in cb:
+            cb["one_core"] = extra_leg(cpu_baseline_one_core)
+        line["cpu_baseline"] = cb
     group.close()
     print(json.dumps(line), flush=True)
     return 0
