@@ -155,6 +155,9 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- helpers
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e datasheet figure
+# Sec. 5: the 8192^3 lattice (20470 steps to half light-crossing) in 1990.51 s on 4096 GPUs
+PAPER_8192_RATE = 8192 ** 3 * 20470 / 1990.51
 STEP_KERNEL_SOURCES = ("ahs_step.cu", "ahs_device.cuh", "ahs_internal.cuh")
 
 
@@ -481,7 +484,11 @@ def run_ours(args, N):
                      "kernel": "step_pair (plain leapfrog step, even N)", "peak_kind": pk_kind,
                      "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
                      "launches": k_n, "measure_kernel_avg_ms": km_ms / max(km_n, 1),
-                     "launch_shape": shape},
+                     "launch_shape": shape, "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
+        # the paper's largest run, another machine's whole-run figure: context only
+        "context": {"paper_8192_run": "8192^3, 20470 steps in 1990.51 s on 4096 P100 GPUs: "
+                                      f"{PAPER_8192_RATE:.3g} site-updates/s, {PAPER_8192_RATE / 4096:.3g} per GPU",
+                    "value_per_gpu_over_paper_per_gpu": value / ws / (PAPER_8192_RATE / 4096)},
         # per period: PERIOD step launches (+1 measurement launch with in-place
         # momenta) and one reduction
         "gpu_launches": args.steps * (PERIOD + (2 if args.momenta_in_place else 1)),
