@@ -212,6 +212,21 @@ int ahs_set_stream(ahs_t *h, void *cuda_stream);
 enum { AHS_KERNEL_STEP = 0, AHS_KERNEL_STEP_MEASURE = 1 };
 int ahs_kernel_time(ahs_t *h, int kind, double *ms_total, int64_t *launches, int reset);
 
+/* ahs_stable_dt -- the largest leapfrog time step that stays stable from eta0 =
+ * tau0 up to conformal time tau_end, times safety (0 < safety <= 1), into *dt.
+ * The staggered leapfrog of Eqs. 7-10 is stable while dt omega_max < 2; omega_max^2
+ * = 12/dx^2 (largest eigenvalue of the lattice Laplacian of Eq. 14 and of the
+ * lattice curl-curl of Eq. 8) + max(lambda0, 2 e0^2) sigma^2 c_max, the Higgs and
+ * gauge masses squared at the largest c = a^{2s} of the run (a = (eta/tau0)^era;
+ * with a core-growth period, s_cg before tau_cg and c continuous there, as
+ * AHS_OPT_CORE_GROWTH_S / _TAU; tau_cg <= tau0 means none).  The paper keeps a
+ * fixed dt = 0.1; this bound matters where s = 1 makes c grow (a^2 in the
+ * radiation era, a^4 in the matter era).  Host arithmetic only, no device call.
+ * Returns AHS_EINVAL for dx <= 0, non-finite couplings, era outside {0,1,2},
+ * tau_end < tau0 or safety outside (0, 1]. */
+int ahs_stable_dt(double dx, double lambda0, double e0, double sigma, double s, int era, double tau0,
+                  double tau_end, double s_cg, double tau_cg, double safety, double *dt);
+
 /* ahs_device_bytes -- device memory of the handle: its field storage (allocated
  * or, before the first ahs_init / ahs_set_fields, to be allocated), measurement
  * partials and records. */
@@ -293,8 +308,10 @@ int ahs_autotune(ahs_t *h);
  * exits; every CTA overwrites its own row, so nothing carries over between calls,
  * but calls that overlap on the GPU (other streams, other threads) share the
  * array and race.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Returns AHS_EINVAL for N outside [4, 1600] (a
+ * address (cudaGetSymbolAddress) with that device current and keeps it for the
+ * life of the process; make that first call before any stream capture.  The kept
+ * address is not valid after cudaDeviceReset (or any other re-creation of the
+ * device's primary context): do not call this entry point after one.  Returns AHS_EINVAL for N outside [4, 1600] (a
  * lattice whose CTAs cannot fit the scratch is rejected the same way), bad
  * parameters or NULL buffers, AHS_ECUDA if a launch fails. */
 #define AHS_NOALLOC_MAX_ROWS 16384

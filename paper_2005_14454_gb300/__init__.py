@@ -26,21 +26,10 @@ PRECISIONS = {"fp32": _abi.AHS_PREC_FP32, "fp32c": _abi.AHS_PREC_FP32_COMPENSATE
 def stable_dt(dx: float, lambda0: float, e0: float, sigma: float, s: float, era: int, tau_end: float,
               tau0: float = 1.0, s_cg: float = 0.0, tau_cg: float = 0.0, safety: float = 0.9) -> float:
     """Largest leapfrog time step that stays stable up to conformal time tau_end,
-    times `safety`: dt omega_max < 2 with omega_max^2 = 12/dx^2 (the largest
-    eigenvalue of the lattice Laplacian and of the lattice curl-curl) plus the
-    larger of the Higgs and gauge masses squared, max(lambda0, 2 e0^2) sigma^2 c,
-    at the largest c = a^{2s} of the run (core-growth schedule included; c is
-    monotonic on each side of tau_cg).  Host arithmetic only."""
-    def c_of(eta):
-        a = (eta / tau0) ** era
-        if tau_cg > tau0 and eta >= tau_cg:
-            acg = (tau_cg / tau0) ** era
-            return acg ** (2 * s_cg) * (a / acg) ** (2 * s)
-        return a ** (2 * (s_cg if tau_cg > tau0 else s))
-    etas = [tau0, tau_end] + ([tau_cg] if tau0 < tau_cg < tau_end else [])
-    c_max = max(c_of(e) for e in etas)
-    w2 = 12.0 / dx ** 2 + max(lambda0, 2.0 * e0 ** 2) * sigma ** 2 * c_max
-    return safety * 2.0 / w2 ** 0.5
+    times `safety` (ahs_stable_dt of the C ABI: dt omega_max < 2, omega_max^2 =
+    12/dx^2 + max(lambda0, 2 e0^2) sigma^2 c at the largest c = a^{2s} of the run,
+    core-growth schedule included)."""
+    return _abi.ahs_stable_dt(dx, lambda0, e0, sigma, s, era, tau0, tau_end, s_cg, tau_cg, safety)
 
 
 class Lattice:

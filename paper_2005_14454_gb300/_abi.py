@@ -34,7 +34,7 @@ EXPORTS = (
     "ahs_batch_create", "ahs_batch_init", "ahs_batch_run", "ahs_batch_records", "ahs_batch_fields",
     "ahs_batch_set_fields", "ahs_batch_step_info", "ahs_batch_set_option", "ahs_batch_get_option",
     "ahs_batch_member_zchunk", "ahs_batch_autotune", "ahs_batch_kernel_time", "ahs_batch_set_stream",
-    "ahs_batch_destroy", "ahs_batch_measure",
+    "ahs_batch_destroy", "ahs_batch_measure", "ahs_stable_dt",
 )
 _NON_INT = ("ahs_create", "ahs_destroy", "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs",
             "ahs_batch_create", "ahs_batch_destroy")
@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ahs_sizeof_obs.restype = sz
     L.ahs_measure_noalloc.argtypes = [i, d, d, d, d, d, d, i, d, d, ctypes.c_int64, vp, vp, vp]
     L.ahs_autotune.argtypes = [H]
+    L.ahs_stable_dt.argtypes = [d, d, d, d, d, i, d, d, d, d, d, ctypes.POINTER(d)]
     i64p = ctypes.POINTER(ctypes.c_int64)
     L.ahs_batch_create.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_uint64), i64p,
                                    d, d, d, d, d, d]
@@ -238,6 +239,13 @@ def ahs_device_bytes(h) -> int:
 def ahs_destroy(h):
     if h:
         lib().ahs_destroy(h)
+
+
+def ahs_stable_dt(dx, lambda0, e0, sigma, s, era, tau0, tau_end, s_cg=0.0, tau_cg=0.0, safety=0.9) -> float:
+    v = ctypes.c_double()
+    check(lib().ahs_stable_dt(dx, lambda0, e0, sigma, s, era, tau0, tau_end, s_cg, tau_cg, safety,
+                              ctypes.byref(v)), "ahs_stable_dt")
+    return v.value
 
 
 def ahs_autotune(h):

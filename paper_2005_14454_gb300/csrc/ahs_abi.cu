@@ -686,6 +686,33 @@ int ahs_autotune(ahs_t *h)
     return ok();
 }
 
+int ahs_stable_dt(double dx, double lambda0, double e0, double sigma, double s, int era, double tau0,
+                  double tau_end, double s_cg, double tau_cg, double safety, double *dt)
+{
+    if (!dt) return fail(AHS_EINVAL, "null argument");
+    if (!(dx > 0) || !std::isfinite(dx) || !std::isfinite(lambda0) || !std::isfinite(e0) || !std::isfinite(sigma) ||
+        !std::isfinite(s) || !std::isfinite(s_cg) || !std::isfinite(tau_cg))
+        return fail(AHS_EINVAL, "dx must be positive and the couplings finite");
+    if (era < 0 || era > 2) return fail(AHS_EINVAL, "era=%d not in {0,1,2}", era);
+    if (!(tau0 > 0) || !std::isfinite(tau0) || !(tau_end >= tau0) || !std::isfinite(tau_end))
+        return fail(AHS_EINVAL, "need 0 < tau0 <= tau_end");
+    if (!(safety > 0) || !(safety <= 1)) return fail(AHS_EINVAL, "safety must be in (0, 1]");
+    eng::LatticeParams lp;
+    lp.dx = dx;
+    lp.lambda0 = lambda0;
+    lp.e0 = e0;
+    lp.sigma = sigma;
+    lp.s = s;
+    lp.era = era;
+    lp.tau0 = tau0;
+    lp.s_cg = s_cg;
+    lp.tau_cg = tau_cg;
+    const double v = eng::stable_dt(&lp, tau_end, safety);
+    if (!(v > 0) || !std::isfinite(v)) return fail(AHS_EINVAL, "no stable step for these parameters");
+    *dt = v;
+    return ok();
+}
+
 int ahs_kernel_time(ahs_t *h, int kind, double *ms, int64_t *launches, int reset)
 {
     if (!h) return fail(AHS_EINVAL, "null handle");

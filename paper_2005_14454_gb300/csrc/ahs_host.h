@@ -26,24 +26,33 @@ struct Scalars {
     double eta, a, delta, omega, c;
 };
 
+// core growth (Sec. 2, after Eq. 6): the width exponent in force at conformal time
+// eta -- s_cg before tau_cg, s after it
+inline double width_exponent(const LatticeParams *h, double eta)
+{
+    return h->tau_cg > h->tau0 && eta < h->tau_cg ? h->s_cg : h->s;
+}
+
+// c = a^{2s} at conformal time eta (a = (eta/eta0)^p), continuous at tau_cg:
+// a^{2 s_cg} before, a_cg^{2 s_cg} (a / a_cg)^{2 s} after
+inline double coupling_factor(const LatticeParams *h, double eta)
+{
+    const double a = std::pow(eta / h->tau0, (double)h->era);
+    if (h->tau_cg > h->tau0 && eta >= h->tau_cg) {
+        const double acg = std::pow(h->tau_cg / h->tau0, (double)h->era);
+        return std::pow(acg, 2.0 * h->s_cg) * std::pow(a / acg, 2.0 * h->s);
+    }
+    return std::pow(a, 2.0 * width_exponent(h, eta));
+}
+
 inline Scalars scalars(const LatticeParams *h, int64_t n)
 {
     Scalars r;
     r.eta = h->tau0 + (double)n * h->dt;
     r.a = std::pow(r.eta / h->tau0, (double)h->era);
     r.delta = 0.5 * h->alpha * (double)h->era * h->dt / r.eta;
-    // core growth (Sec. 2, after Eq. 6): exponent s_cg before tau_cg and s after
-    // it, in omega and in c, with c continuous at tau_cg:
-    // c = a^{2 s_cg} before, a_cg^{2 s_cg} (a / a_cg)^{2 s} after
-    const bool grow = h->tau_cg > h->tau0;
-    const double s = grow && r.eta < h->tau_cg ? h->s_cg : h->s;
-    r.omega = r.delta * (1.0 - s);
-    if (grow && r.eta >= h->tau_cg) {
-        const double acg = std::pow(h->tau_cg / h->tau0, (double)h->era);
-        r.c = std::pow(acg, 2.0 * h->s_cg) * std::pow(r.a / acg, 2.0 * h->s);
-    } else {
-        r.c = std::pow(r.a, 2.0 * s);
-    }
+    r.omega = r.delta * (1.0 - width_exponent(h, r.eta));
+    r.c = coupling_factor(h, r.eta);
     if (h->cooling > 0.0) {
         // cooling (the artificial damping period of Sec. 2): static background with
         // the same constant Crank-Nicolson damping on both momenta
@@ -58,7 +67,7 @@ inline StepCoef coefficients(const LatticeParams *h, int64_t n)
 {
     const Scalars S = scalars(h, n);
     const double dx = h->dx, dt = h->dt;
-    StepCoef k;
+    StepCoef k{};
     k.cpi = (float)((1.0 - S.delta) / (1.0 + S.delta));
     k.kpi_lap = (float)(dt / ((1.0 + S.delta) * dx * dx));
     k.kpi_pot = (float)(dt * 0.5 * h->lambda0 * S.c / (1.0 + S.delta));
@@ -85,7 +94,7 @@ inline StepCoef64 coefficients64(const LatticeParams *h, int64_t n)
 {
     const Scalars S = scalars(h, n);
     const double dx = h->dx, dt = h->dt;
-    StepCoef64 k;
+    StepCoef64 k{};
     k.cpi = (1.0 - S.delta) / (1.0 + S.delta);
     k.kpi_lap = dt / ((1.0 + S.delta) * dx * dx);
     k.kpi_pot = dt * 0.5 * h->lambda0 * S.c / (1.0 + S.delta);
@@ -110,7 +119,7 @@ inline StepCoef64 coefficients64(const LatticeParams *h, int64_t n)
 inline ObsScalars obs_scalars(const LatticeParams *h, int64_t n)
 {
     const Scalars S = scalars(h, n);
-    ObsScalars o;
+    ObsScalars o{};
     o.step = n;
     o.tau = S.eta;
     o.a = S.a;
@@ -119,6 +128,26 @@ inline ObsScalars obs_scalars(const LatticeParams *h, int64_t n)
     o.volume = std::pow((double)h->N * h->dx, 3.0);
     o.mu = 2.0 * 3.141592653589793238 * h->sigma * h->sigma;
     return o;
+}
+
+// Largest stable leapfrog step up to conformal time tau_end, times `safety`: the
+// scheme is stable while dt omega_max < 2, with omega_max^2 = 12/dx^2 (the largest
+// eigenvalue of the lattice Laplacian, and of the lattice curl-curl) plus the larger
+// mass squared, max(lambda0, 2 e0^2) sigma^2 c, at the largest c of the run.  c is
+// monotonic in eta on each side of tau_cg, so its largest value is at tau0, tau_end
+// or tau_cg.
+inline double stable_dt(const LatticeParams *h, double tau_end, double safety)
+{
+    double c_max = coupling_factor(h, h->tau0);
+    const double c_end = coupling_factor(h, tau_end);
+    if (c_end > c_max) c_max = c_end;
+    if (h->tau_cg > h->tau0 && h->tau_cg < tau_end) {
+        const double c_cg = coupling_factor(h, h->tau_cg);
+        if (c_cg > c_max) c_max = c_cg;
+    }
+    const double m2 = (h->lambda0 > 2.0 * h->e0 * h->e0 ? h->lambda0 : 2.0 * h->e0 * h->e0) * h->sigma * h->sigma;
+    const double w2 = 12.0 / (h->dx * h->dx) + m2 * c_max;
+    return safety * 2.0 / std::sqrt(w2);
 }
 
 }  // namespace eng

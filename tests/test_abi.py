@@ -86,3 +86,17 @@ def test_binding_constants_match_the_header(abi):
             continue
         assert getattr(abi, name) == value, name
     assert consts["AHS_OPT_MOMENTA_IN_PLACE"] == 12
+
+
+@pytest.mark.parametrize("args", [
+    (0.0, 2.0, 1.0, 1.0, 0.0, 1, 1.0, 10.0, 0.0, 0.0, 0.9),           # dx <= 0
+    (0.5, 2.0, 1.0, 1.0, 0.0, 3, 1.0, 10.0, 0.0, 0.0, 0.9),           # unknown era
+    (0.5, 2.0, 1.0, 1.0, 0.0, 1, 1.0, 0.5, 0.0, 0.0, 0.9),            # tau_end < tau0
+    (0.5, 2.0, 1.0, 1.0, 0.0, 1, 1.0, 10.0, 0.0, 0.0, 1.5),           # safety > 1
+    (0.5, float("inf"), 1.0, 1.0, 0.0, 1, 1.0, 10.0, 0.0, 0.0, 0.9),  # non-finite coupling
+])
+def test_stable_dt_rejects_bad_arguments(abi, args):
+    v = ctypes.c_double(-1.0)
+    assert abi.lib().ahs_stable_dt(*args, ctypes.byref(v)) == abi.AHS_EINVAL
+    assert v.value == -1.0
+    assert abi.lib().ahs_stable_dt(0.5, 2.0, 1.0, 1.0, 0.0, 1, 1.0, 10.0, 0.0, 0.0, 0.9, None) == abi.AHS_EINVAL

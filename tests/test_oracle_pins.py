@@ -541,3 +541,11 @@ def test_stable_time_step_bound(orc):
     # core growth: c peaks at the end of the run, below the constant-s = 1 value
     assert stable_dt(0.5, 2.0, 1.0, 1.0, 1.0, 1, 16.0, s_cg=-1.0, tau_cg=4.0) > \
         stable_dt(0.5, 2.0, 1.0, 1.0, 1.0, 1, 16.0)
+    # radiation era, s_cg = -1 until eta = 4, then s = 1 with c continuous:
+    # c(4) = 4^-2 and c(16) = 4^-2 (16/4)^2 = 1 = c(1), so the bound is the s = 0 one;
+    # with s = 1 throughout c(16) = 16^2
+    assert stable_dt(0.5, 2.0, 1.0, 1.0, 1.0, 1, 16.0, s_cg=-1.0, tau_cg=4.0) == \
+        pytest.approx(0.9 * 2 / math.sqrt(48 + 2))
+    assert stable_dt(0.5, 2.0, 1.0, 1.0, 1.0, 1, 16.0) == pytest.approx(0.9 * 2 / math.sqrt(48 + 2 * 256))
+    # the gauge mass 2 e0^2 sigma^2 decides when it is the larger one
+    assert stable_dt(0.5, 1.0, 2.0, 1.0, 0.0, 0, 2.0) == pytest.approx(0.9 * 2 / math.sqrt(48 + 8))
