@@ -10,7 +10,7 @@
 // result, and the only scratch the measurement needs -- one row of FP64 partial
 // sums per CTA -- lives in the static device array below, which every GPU that
 // loads this library holds until the process exits.
-#include "ahs_internal.cuh"
+#include "ahs_host.h"
 
 #include <cmath>
 #include <cstdio>
@@ -83,34 +83,22 @@ extern "C" int ahs_measure_noalloc(int N, double dx, double dt, double lambda0, 
     void *scratch = nullptr;
     if (int r = scratch_address(&scratch)) return r;
 
-    // FP64 scalars of step n (Eqs. 7, 8, 11, 12) and the measurement factors
-    auto scal = [&](int64_t n, double &eta, double &a, double &delta, double &omega, double &c) {
-        eta = tau0 + (double)n * dt;
-        a = std::pow(eta / tau0, (double)era);
-        delta = 0.5 * alpha * (double)era * dt / eta;
-        omega = delta * (1.0 - s);
-        c = std::pow(a, 2.0 * s);
-    };
-    double eta, a, delta, omega, c, etap, ap, deltap, omegap, cp;
-    scal(step, eta, a, delta, omega, c);
-    scal(step - 1, etap, ap, deltap, omegap, cp);
-    StepCoef k;
-    k.cpi = (float)((1.0 - delta) / (1.0 + delta));
-    k.kpi_lap = (float)(dt / ((1.0 + delta) * dx * dx));
-    k.kpi_pot = (float)(dt * 0.5 * lambda0 * c / (1.0 + delta));
-    k.sigma2 = (float)(sigma * sigma);
-    k.ce = (float)((1.0 - omega) / (1.0 + omega));
-    k.ke_curl = (float)(dt / ((1.0 + omega) * dx * dx * dx));
-    k.ke_cur = (float)(dt * 2.0 * e0 * e0 * c / ((1.0 + omega) * dx));
-    k.dphi = (float)dt;
-    k.dtheta = (float)(dt * dx);
-    k.wrap = 0;
-    k.m_grad = (float)(1.0 / (dx * dx));
-    k.m_pot = (float)(0.25 * lambda0 * c);
-    k.m_el = (float)(1.0 / (2.0 * e0 * e0 * c));
-    k.m_mag = (float)(1.0 / (e0 * e0 * c * dx * dx * dx * dx));
-    k.m_gauss = (float)(2.0 * e0 * e0 * cp * (1.0 + deltap) / (1.0 + omegap));
-    k.inv_dx = (float)(1.0 / dx);
+    // the coefficients and record scalars of step n from the same FP64 helpers the
+    // handle-based entry points use (Eqs. 7, 8, 11, 12), so the record equals the
+    // one ahs_measure gives for the same launch shape
+    LatticeParams lp;
+    lp.N = N;
+    lp.dx = dx;
+    lp.dt = dt;
+    lp.lambda0 = lambda0;
+    lp.e0 = e0;
+    lp.sigma = sigma;
+    lp.s = s;
+    lp.era = era;
+    lp.alpha = alpha;
+    lp.tau0 = tau0;
+    const StepCoef k = coefficients(&lp, step);
+    const ObsScalars o = obs_scalars(&lp, step);
 
     const size_t V = (size_t)N * N * N;
     StepPtrs p = {};
@@ -124,15 +112,6 @@ extern "C" int ahs_measure_noalloc(int N, double dx, double dt, double lambda0, 
     p.ex = fields + 7 * V;
     p.ey = fields + 8 * V;
     p.ez = fields + 9 * V;
-
-    ObsScalars o;
-    o.step = step;
-    o.tau = eta;
-    o.a = a;
-    o.dx = dx;
-    o.sites = (double)V;
-    o.volume = std::pow((double)N * dx, 3.0);
-    o.mu = 2.0 * 3.141592653589793238 * sigma * sigma;
 
     cudaStream_t st = (cudaStream_t)stream;
     double *partials = static_cast<double *>(scratch);

@@ -4,6 +4,8 @@ the same seeds bit for bit, stop at their own last step, and match the oracle.""
 import numpy as np
 import pytest
 
+from parity import field_errors, site_errors
+
 pytestmark = pytest.mark.gpu
 
 PARAMS = dict(dx=0.5, dt=0.1, lambda0=2.0, e0=1.0, sigma=1.0)
@@ -73,9 +75,10 @@ def test_batch_member_matches_oracle(pkg, orc):
             ref = F0[i].copy()
             orc.run(orc.Params(N=N, era=era, **PARAMS), 0, 10, ref)
             got = b.state(i).astype(np.float64)
-            for sl in (slice(0, 2), slice(2, 4), slice(7, 10)):
-                err = np.linalg.norm(got[sl] - ref[sl]) / np.linalg.norm(ref[sl])
-                assert err < 1e-5
+            err = field_errors(got, ref)
+            assert max(err.values()) < 1e-5, err
+            se = site_errors(got, ref)
+            assert max(se.values()) < 5e-6, se
 
 
 def test_batch_autotune_keeps_results(pkg):

@@ -2,7 +2,8 @@
 
 Tolerances (float32 storage and arithmetic against FP64):
 * fields after 10 leapfrog steps from identical float32 states: relative L2 error
-  <= 1e-5 per field group (phi, Pi, theta via exp(-i theta), E);
+  <= 1e-5 per field group (phi, Pi, theta via exp(-i theta), E), and at every
+  single site an error <= 5e-6 of the group's RMS (tests/parity.py);
 * windings on identical snapshots: bit-exact, per plaquette;
 * observables on identical snapshots: sums of non-negative site terms to 2e-5
   relative; signed or ratio observables to 2e-4 relative (per-site float32
@@ -41,17 +42,21 @@ def oparams(orc, N, era=1, s=0.0, **kw):
     return orc.Params(N=N, era=era, s=s, **p)
 
 
-def rel(a, b):
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+from parity import field_errors, rel, site_errors, worst_site  # noqa: E402
+
+# Per-site bound of the 10-step field checks: the largest error at any single site,
+# on the scale of the field group's RMS (see parity.site_errors).  Ten float32 steps
+# leave errors of a few 1e-7 of that scale at a typical site (the L2 measure); the
+# worst of up to 3e5 sites sits a few times above the typical one.
+SITE_TOL = 5e-6
 
 
-def field_errors(got, ref):
-    return {
-        "phi": rel(got[0:2], ref[0:2]),
-        "Pi": rel(got[2:4], ref[2:4]),
-        "theta": np.linalg.norm(np.exp(-1j * got[4:7]) - np.exp(-1j * ref[4:7])) / max(np.linalg.norm(ref[4:7]), 1e-3 * math.sqrt(ref[4:7].size)),
-        "E": rel(got[7:10], ref[7:10]),
-    }
+def assert_fields_match(got, ref):
+    err = field_errors(got, ref)
+    assert max(err.values()) < 1e-5, err
+    se = site_errors(got, ref)
+    bad = {k: (v, worst_site(got, ref, k)) for k, v in se.items() if not v < SITE_TOL}
+    assert not bad, bad
 
 
 # ------------------------------------------------------------------ init
@@ -89,8 +94,7 @@ def test_ten_steps_match_oracle(eng, orc, N, era, s):
         assert lat.n == 10
     ref = F0.copy()
     orc.run(oparams(orc, N, era=era, s=s), 0, 10, ref)
-    err = field_errors(got, ref)
-    assert max(err.values()) < 1e-5, err
+    assert_fields_match(got, ref)
 
 
 @pytest.mark.parametrize("N", [20, 40, 64])
@@ -128,8 +132,7 @@ def test_perturbed_state_with_gauge_fields(eng, orc):
         got = lat.state().astype(np.float64)
     ref = F0.copy()
     orc.run(oparams(orc, N, era=2), 3, 10, ref)
-    err = field_errors(got, ref)
-    assert max(err.values()) < 1e-5, err
+    assert_fields_match(got, ref)
 
 
 @pytest.mark.parametrize("span", [3.0, 50.0, 9000.0])
@@ -310,28 +313,97 @@ def test_bad_buffers_rejected(eng):
 
 
 # ------------------------------------------------------------------ full size
-def test_full_size_sampled_sites(eng, orc):
-    """1024^3 in the launch configuration the benchmark times: one step from the
-    random-phase start and one from a later state, checked at sampled sites
-    against the oracle run on the 5^3 periodic neighbourhood of each site (the
-    update of a site reads only its nearest and next-nearest neighbours)."""
-    N = 1024
-    rng = np.random.default_rng(0)
-    sites = [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(12)]
+def sampled_sites(N, count, seed):
+    rng = np.random.default_rng(seed)
+    sites = [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(count)]
+    # corners, and sites on both sides of the 192-plane z-chunk boundaries of 1024^3
     sites += [(0, 0, 0), (N - 1, N - 1, N - 1), (0, N - 1, 511), (N - 1, 0, 0)]
-    from paper_2005_14454_gb300 import AHS_FIELD_ALL
-    with lattice(eng, N, measure_every=0) as lat:
-        lat.init(1)
-        lat.step(3)
-        before = [lat.box(AHS_FIELD_ALL, x - 2, y - 2, z - 2, 5, 5, 5).astype(np.float64) for (x, y, z) in sites]
-        lat.step(1)
-        after = [lat.box(AHS_FIELD_ALL, x, y, z, 1, 1, 1).astype(np.float64)[:, 0, 0, 0] for (x, y, z) in sites]
+    sites += [(5, 77, 191), (64, 63, 192), (1023, 8, 383), (31, 7, 384), (700, 900, 767), (1, 1, 768)]
+    return [(x % N, y % N, z % N) for (x, y, z) in sites]
+
+
+def check_sites(orc, before, after, n):
     p = oparams(orc, 5)
     for B, A in zip(before, after):
         ref = B.copy()
-        orc.run(p, 3, 1, ref)
+        orc.run(p, n, 1, ref)
         r = ref[:, 2, 2, 2]
         assert np.allclose(A, r, rtol=2e-6, atol=2e-6), (A, r)
+
+
+def test_full_size_sampled_sites(eng, orc):
+    """1024^3 in the launch configuration the benchmark times: a plain step (the
+    paired kernel) and a measuring step (the fused measurement kernel, 32 x 8 tiles,
+    192-plane z-chunks, 24576 rows of partial sums), each checked at sampled sites
+    against the oracle run on the 5^3 periodic neighbourhood of each site (the update
+    of a site reads only its nearest and next-nearest neighbours).  The record of the
+    measuring step is checked by properties that hold at any size: it equals
+    ahs_measure at the same launch shape bit for bit, its winding count equals the
+    sum of |W| of the separate winding kernel, and a measurement at another z-chunk
+    (64 planes, 65536 rows) agrees up to the grouping of the sums."""
+    N = 1024
+    sites = sampled_sites(N, 12, 0)
+    from paper_2005_14454_gb300 import AHS_FIELD_ALL
+    from paper_2005_14454_gb300._abi import AHS_OPT_ZCHUNK
+
+    def boxes(lat, w):
+        o = -(w // 2)
+        return [lat.box(AHS_FIELD_ALL, x + o, y + o, z + o, w, w, w).astype(np.float64) for (x, y, z) in sites]
+
+    with lattice(eng, N, measure_every=10) as lat:
+        assert int(lat.n) == 0
+        lat.init(1)
+        lat.step(3)
+        before = boxes(lat, 5)
+        lat.step(1)                                # n = 3: plain step
+        check_sites(orc, before, [b[:, 0, 0, 0] for b in boxes(lat, 1)], 3)
+        lat.step(6)
+        assert lat.n == 10
+        assert int(__import__("paper_2005_14454_gb300")._abi.ahs_get_option(lat.h, AHS_OPT_ZCHUNK)) == 192
+        lat.records()
+        before = boxes(lat, 5)
+        standalone = lat.measure()
+        W, n_wind = lat.windings()
+        del W
+        lat.set_option(AHS_OPT_ZCHUNK, 64)
+        other = lat.measure()
+        lat.set_option(AHS_OPT_ZCHUNK, 0)
+        lat.step(1)                                # n = 10: measuring step
+        rec = lat.records()
+        check_sites(orc, before, [b[:, 0, 0, 0] for b in boxes(lat, 1)], 10)
+    assert [r["step"] for r in rec] == [10]
+    assert rec[0] == standalone
+    assert rec[0]["n_wind"] == n_wind == other["n_wind"] > 0
+    assert rec[0]["gauss_max"] == other["gauss_max"]
+    assert rec[0]["nonfinite"] == 0
+    for k in SUMS:
+        assert rec[0][k] == pytest.approx(other[k], rel=1e-5), k
+    for k in SIGNED:
+        assert rec[0][k] == pytest.approx(other[k], rel=2e-4), k
+
+
+def test_measure_at_benchmark_zchunk_matches_oracle(eng, orc):
+    """The fused measurement at the z-chunk the 1024^3 benchmark uses (192 planes),
+    on a 640^3 lattice (three full chunks and a ragged one of 64; 6400 rows of
+    partial sums) against the oracle's measurement of the same snapshot: windings
+    bit-exact, sums and ratios to the tolerances of the identical-snapshot test."""
+    from paper_2005_14454_gb300._abi import AHS_OPT_ZCHUNK
+    N, steps = 640, 10
+    with lattice(eng, N, era=1) as lat:
+        lat.init(11)
+        lat.step(steps)
+        lat.set_option(AHS_OPT_ZCHUNK, 192)
+        obs = lat.measure()
+        snap = lat.state()
+    o = orc.measure(oparams(orc, N), steps, snap.astype(np.float64))
+    del snap
+    assert obs["n_wind"] == o["n_wind"] > 0
+    assert obs["nonfinite"] == o["nonfinite"] == 0
+    for k in SUMS:
+        assert obs[k] == pytest.approx(o[k], rel=2e-5), k
+    for k in SIGNED:
+        assert obs[k] == pytest.approx(o[k], rel=2e-4), k
+    assert abs(obs["gauss_rms"] - o["gauss_rms"]) < 1e-6 * (1.0 + abs(o["gauss_rms"]))
 
 
 # ------------------------------------------------------------------ core growth
@@ -362,6 +434,9 @@ def test_core_growth_matches_oracle(eng, orc, era):
     orc.run(p, n, 18 - n, ref)
     err = field_errors(got, ref)
     assert max(err.values()) < 1e-5, err
+    # 18 steps through the switch of c: every site within 1e-5 of its field's RMS
+    se = site_errors(got, ref)
+    assert max(se.values()) < 1e-5, se
 
 
 # ------------------------------------------------------------------ cooling, straight strings
@@ -388,6 +463,8 @@ def test_cooled_vortex_pair_matches_oracle(eng, orc):
     orc.run(oparams(orc, N, cool=0.5), 0, 200, ref)
     err = field_errors(got, ref)
     assert err["phi"] < 1e-5 and err["theta"] < 1e-5, err
+    se = site_errors(got, ref)
+    assert se["phi"] < 1e-5 and se["theta"] < 1e-5, se
     # the momenta are damped towards zero: compare them on the scale of phi
     scale = np.linalg.norm(ref[0:2])
     assert np.linalg.norm(got[2:4] - ref[2:4]) / scale < 1e-5
