@@ -84,8 +84,23 @@ enum {
                                   artificial damping period Sec. 2 mentions); 0 = off       */
     AHS_OPT_MOMENTA_IN_PLACE = 12, /* 1: keep one copy of Pi and E and update it in place */
     AHS_OPT_CORE_GROWTH_S = 13,   /* s of the core-growth period (see below); default 0    */
-    AHS_OPT_CORE_GROWTH_TAU = 14  /* end eta_cg of the period; <= eta0 (default): none     */
+    AHS_OPT_CORE_GROWTH_TAU = 14, /* end eta_cg of the period; <= eta0 (default): none     */
+    AHS_OPT_STEPS_PER_PASS = 15   /* 1 (default) or 2: temporal blocking, see below          */
 };
+
+/* AHS_OPT_STEPS_PER_PASS = 2 (float32 precision with double-buffered momenta only).
+ * Two consecutive plain steps (neither of them a measuring step) run as one launch
+ * that reads every field once at n and writes it once at n+2 (40 + 40 bytes per
+ * two site-updates instead of 80 + 80, the paper's remark that the kernels are
+ * memory bound, Sec. 5).  The second step of a tile needs the first step's phi and
+ * theta on a one-site ring, so the first step is computed on the tile plus that
+ * ring (34 x 10 sites for a 32 x 8 tile) from link phases over a two-site ring:
+ * about 16% more arithmetic per site-update.  Fields are those of two single
+ * steps.  A measuring step, or a step left over at the end of an ahs_step call,
+ * runs alone.  The launch uses 32 x 8 tiles whatever AHS_OPT_TILE_Y says, and the
+ * z-chunk of AHS_OPT_ZCHUNK.  Setting it with another precision or with in-place
+ * momenta (where the first step of a neighbouring tile would overwrite momenta the
+ * ring still reads) returns AHS_EINVAL, as does changing those while it is 2. */
 
 /* Core growth (Sec. 2, after Eq. 6): a negative s makes the comoving string width
  * grow, so that the true equations (s = 1) can later shrink it without it falling
@@ -207,9 +222,11 @@ int ahs_set_stream(ahs_t *h, void *cuda_stream);
 /* ahs_kernel_time -- with AHS_OPT_PROFILE on: total device time (ms, CUDA
  * events recorded on the handle's stream around each launch) and number of
  * launches of the step kernel since the last reset.  kind selects the plain
- * step kernel (AHS_KERNEL_STEP) or the step kernel with the fused measurement
- * (AHS_KERNEL_STEP_MEASURE); reset != 0 zeroes that counter after reading. */
-enum { AHS_KERNEL_STEP = 0, AHS_KERNEL_STEP_MEASURE = 1 };
+ * step kernel (AHS_KERNEL_STEP), the step kernel with the fused measurement
+ * (AHS_KERNEL_STEP_MEASURE) or the two-step kernel of AHS_OPT_STEPS_PER_PASS = 2
+ * (AHS_KERNEL_STEP_PAIR, one launch per two steps); reset != 0 zeroes that
+ * counter after reading. */
+enum { AHS_KERNEL_STEP = 0, AHS_KERNEL_STEP_MEASURE = 1, AHS_KERNEL_STEP_PAIR = 2 };
 int ahs_kernel_time(ahs_t *h, int kind, double *ms_total, int64_t *launches, int reset);
 
 /* ahs_stable_dt -- the largest leapfrog time step that stays stable from eta0 =

@@ -38,7 +38,7 @@ class Lattice:
     def __init__(self, N: int, dx: float = 0.5, dt: float = 0.1, lambda0: float = 2.0,
                  e0: float = 1.0, sigma: float = 1.0, s: float = 0.0, era=AHS_RADIATION,
                  measure_every: int = 10, stream: int | None = None, precision=None,
-                 momenta_in_place: bool = False, core_growth=None):
+                 momenta_in_place: bool = False, core_growth=None, steps_per_pass: int = 1):
         era = ERAS.get(era, era) if isinstance(era, str) else era
         self.N = N
         self.params = dict(N=N, dx=dx, dt=dt, lambda0=lambda0, e0=e0, sigma=sigma, s=s, era=era)
@@ -52,6 +52,8 @@ class Lattice:
         if core_growth is not None:          # (s_cg, tau_cg)
             _abi.ahs_set_option(self.h, _abi.AHS_OPT_CORE_GROWTH_S, core_growth[0])
             _abi.ahs_set_option(self.h, _abi.AHS_OPT_CORE_GROWTH_TAU, core_growth[1])
+        if steps_per_pass != 1:
+            _abi.ahs_set_option(self.h, _abi.AHS_OPT_STEPS_PER_PASS, steps_per_pass)
         if stream is not None:
             _abi.ahs_set_stream(self.h, stream)
 
@@ -122,7 +124,7 @@ class Lattice:
     _SAVED_OPTIONS = ("AHS_OPT_STEP", "AHS_OPT_ALPHA", "AHS_OPT_TAU0", "AHS_OPT_WRAP_THETA",
                       "AHS_OPT_MEASURE_EVERY", "AHS_OPT_PRECISION", "AHS_OPT_COOLING",
                       "AHS_OPT_MOMENTA_IN_PLACE", "AHS_OPT_CORE_GROWTH_S", "AHS_OPT_CORE_GROWTH_TAU",
-                      "AHS_OPT_TILE_Y", "AHS_OPT_ZCHUNK")
+                      "AHS_OPT_TILE_Y", "AHS_OPT_ZCHUNK", "AHS_OPT_STEPS_PER_PASS")
 
     def save(self, path: str):
         """Write a restart file (numpy .npz): the fields at the current time level in

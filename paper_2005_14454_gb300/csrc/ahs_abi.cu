@@ -77,9 +77,10 @@ struct ahs : eng::LatticeParams {
     std::vector<ahs_obs_t> log;
 
     cudaStream_t stream = nullptr;
+    int steps_per_pass = 1;          // 2: pairs of plain steps as one launch
     std::vector<cudaEvent_t> ev;     // profiling event pool (pairs)
-    double prof_ms[2] = {0.0, 0.0};  // [plain step, measuring step]
-    int64_t prof_launches[2] = {0, 0};
+    double prof_ms[3] = {0.0, 0.0, 0.0};  // [plain step, measuring step, two-step launch]
+    int64_t prof_launches[3] = {0, 0, 0};
 
     // index of plane f of buffer buf in the allocation
     size_t plane_index(int buf, int f) const
@@ -399,6 +400,7 @@ int ahs_set_option(ahs_t *h, int key, double v)
             return fail(AHS_EINVAL, "precision must be AHS_PREC_FP32, _FP32_COMPENSATED or _FP64");
         if ((int)v == h->precision) return ok();
         if (h->inplace && v != AHS_PREC_FP32) return fail(AHS_EINVAL, "in-place momenta need float32 precision");
+        if (h->steps_per_pass == 2) return fail(AHS_EINVAL, "two steps per pass need float32 precision");
         if (int r = set_device(h)) return r;
         if (h->stream) cudaStreamSynchronize(h->stream);
         else cudaDeviceSynchronize();
@@ -422,6 +424,7 @@ int ahs_set_option(ahs_t *h, int key, double v)
         if (v != 0 && v != 1) return fail(AHS_EINVAL, "momenta_in_place must be 0 or 1");
         if ((int)v == h->inplace) return ok();
         if (v == 1 && h->precision != AHS_PREC_FP32) return fail(AHS_EINVAL, "in-place momenta need float32 precision");
+        if (v == 1 && h->steps_per_pass == 2) return fail(AHS_EINVAL, "two steps per pass need double-buffered momenta");
         if (int r = set_device(h)) return r;
         if (h->stream) cudaStreamSynchronize(h->stream);
         else cudaDeviceSynchronize();
@@ -429,6 +432,12 @@ int ahs_set_option(ahs_t *h, int key, double v)
         reset_fields(h);
         return ok();
     }
+    case AHS_OPT_STEPS_PER_PASS:
+        if (v != 1 && v != 2) return fail(AHS_EINVAL, "steps_per_pass must be 1 or 2");
+        if (v == 2 && (h->precision != AHS_PREC_FP32 || h->inplace))
+            return fail(AHS_EINVAL, "two steps per pass need float32 precision and double-buffered momenta");
+        h->steps_per_pass = (int)v;
+        return ok();
     case AHS_OPT_N:
         return fail(AHS_EINVAL, "N is read only");
     default:
@@ -452,6 +461,7 @@ int ahs_get_option(ahs_t *h, int key, double *v)
     case AHS_OPT_MOMENTA_IN_PLACE: *v = h->inplace; break;
     case AHS_OPT_CORE_GROWTH_S: *v = h->s_cg; break;
     case AHS_OPT_CORE_GROWTH_TAU: *v = h->tau_cg; break;
+    case AHS_OPT_STEPS_PER_PASS: *v = h->steps_per_pass; break;
     case AHS_OPT_TILE_Y: *v = h->precision == AHS_PREC_FP64 ? 8 : step_shape(h->N, h->tile_y, h->zchunk).by; break;
     case AHS_OPT_ZCHUNK: *v = step_shape(h->N, h->tile_y, h->zchunk).dz; break;
     default: return fail(AHS_EINVAL, "unknown option %d", key);
@@ -474,16 +484,28 @@ int ahs_step(ahs_t *h, int nsteps)
     if (int r = ensure_partials(h, launch_blocks(h))) return r;
     size_t nev = 0;
     int ri = 0;
-    std::vector<char> kind;          // per event pair: 1 if the launch measured
+    std::vector<char> kind;          // per event pair: the AHS_KERNEL_* kind of the launch
+    auto measures = [h](int64_t n) { return h->measure_every > 0 && (n % h->measure_every == 0); };
     for (int i = 0; i < nsteps; ++i) {
-        const bool meas = h->measure_every > 0 && (h->n % h->measure_every == 0);
+        const bool meas = measures(h->n);
+        const bool pair = h->steps_per_pass == 2 && !meas && i + 1 < nsteps && !measures(h->n + 1);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->profile) {
             e0 = event_at(h, nev++);
             e1 = event_at(h, nev++);
-            kind.push_back(meas ? 1 : 0);
+            kind.push_back(pair ? AHS_KERNEL_STEP_PAIR : meas ? AHS_KERNEL_STEP_MEASURE : AHS_KERNEL_STEP);
             if (!e0 || !e1) return fail(AHS_ECUDA, "cudaEventCreate failed");
             CU(cudaEventRecord(e0, h->stream));
+        }
+        if (pair) {
+            // steps n and n+1 in one pass: buffer cur (time n) -> the other (n+2)
+            CU(launch_step_two(pointers(h), coefficients(h, h->n), coefficients(h, h->n + 1), h->N,
+                               step_shape(h->N, 8, h->zchunk).dz, h->stream));
+            if (h->profile) CU(cudaEventRecord(e1, h->stream));
+            h->cur = 1 - h->cur;
+            h->n += 2;
+            ++i;
+            continue;
         }
         const int nb = launch_blocks(h);
         if (meas && h->inplace) {
@@ -716,7 +738,8 @@ int ahs_stable_dt(double dx, double lambda0, double e0, double sigma, double s, 
 int ahs_kernel_time(ahs_t *h, int kind, double *ms, int64_t *launches, int reset)
 {
     if (!h) return fail(AHS_EINVAL, "null handle");
-    if (kind != AHS_KERNEL_STEP && kind != AHS_KERNEL_STEP_MEASURE) return fail(AHS_EINVAL, "unknown kernel kind %d", kind);
+    if (kind != AHS_KERNEL_STEP && kind != AHS_KERNEL_STEP_MEASURE && kind != AHS_KERNEL_STEP_PAIR)
+        return fail(AHS_EINVAL, "unknown kernel kind %d", kind);
     if (ms) *ms = h->prof_ms[kind];
     if (launches) *launches = h->prof_launches[kind];
     if (reset) {

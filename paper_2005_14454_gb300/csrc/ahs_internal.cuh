@@ -97,6 +97,11 @@ cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepS
 // measuring steps whose launch overwrites E in place.
 cudaError_t launch_gauss(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, double *partials,
                          cudaStream_t st);
+// Two plain float32 steps n -> n+2 in one pass (temporal blocking): k1, k2 are
+// the coefficients of steps n and n+1; reads the time-n buffer, writes the other.
+// 32 x 8 tiles, Dz planes per CTA.
+cudaError_t launch_step_two(const StepPtrs &p, const StepCoef &k1, const StepCoef &k2, int N, int Dz,
+                            cudaStream_t st);
 cudaError_t launch_step64(const StepPtrs64 &p, const StepCoef64 &k, int N, const StepShape &sh, bool measure,
                           bool store, double *partials, cudaStream_t st);
 cudaError_t launch_init_fp64(double *pr, double *pim, int N, uint64_t seed, double sigma, cudaStream_t st);
