@@ -18,10 +18,15 @@
 // Values a site needs from its z-1 neighbour (phi, V_z, sin alpha_xz/yz, E_z) are
 // carried in registers from the previous plane; in-plane neighbours come from
 // shared memory.  Every link phase and plaquette of the tile is computed once.
-// Two CTA barriers per plane (after A and after B): the link phases rotate
-// through three plane buffers, so phase A of plane z+1 never writes a buffer
-// that a thread still in phase C of plane z-1 reads, and the barrier after A
-// orders every other shared array (each is written in B and read in C).
+// One CTA barrier per plane (between B and C).  Phase B reads the link phases of
+// plane z+1 only at sites the same thread wrote in phase A (its own column, and
+// the ring sites of the backward-ring plaquettes and forward-ring link phases,
+// which go to the thread that loaded them); everything else it reads is at least
+// a plane old.  The link phases rotate through three plane buffers, so phase A of
+// plane z+1 never writes a buffer a thread still in phase C of plane z-1 reads,
+// and the arrays written in B and read in C (plaquette sines, measurement data)
+// alternate between two buffers, so phase B of plane z+1 never writes the one a
+// thread still in phase C of plane z reads.
 // Tile coordinates wrap modulo N, so ragged tiles and N < 32 need no special path.
 // Site offsets are 32-bit (the handle limits N^3 below 2^32).
 // Kernels: step_tiled (any step, float32 and compensated, one site per thread),
@@ -41,19 +46,19 @@ struct Tile {
     static constexpr int SX = BX + 1, SY = BY + 1, NS = SX * SY;  // plaquettes: [-1, BX) x [-1, BY)
     static constexpr int YX = BX + 1, YY = BY + 1, NYW = YX * YY; // link phases Y: [0, BX] x [0, BY]
     static constexpr int NHA = 2 * RX + 2 * BY;                    // ring sites of phase A
-    static constexpr int NHB = BX + BY;                            // backward ring sites of phase B
-    static_assert(NHA <= NT && NHB <= NT, "ring items must fit one pass of the CTA");
+    static_assert(NHA <= NT, "ring items must fit one pass of the CTA");
 
     using V2 = typename Real<R>::V2;
     struct Plane {
         V2 vx[NR], vy[NR], vz[NR], ph[NR];
     };
+    // written in phase B, read in phase C: two buffers, by the parity of the plane
     struct Smem {
         Plane pl[3];
-        R sxy[NS], sxz[NS], syz[NS];
+        R sxy[2][NS], sxz[2][NS], syz[2][NS];
         // measurement steps only
-        int yx[NYW], yy[NYW], yz[NYW];
-        R ex[NS], ey[NS];
+        int yx[2][NYW], yy[2][NYW], yz[2][NYW];
+        R ex[2][NS], ey[2][NS];
     };
     static constexpr size_t kStepBytes = offsetof(Smem, yx);
     static constexpr size_t kMeasureBytes = sizeof(Smem);
@@ -90,17 +95,19 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         else { hax = T::BX; hay = t - 2 * T::RX - BY; }
     }
     const uint32_t haoff = (uint32_t)wrapN(x0 + hax, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hay, N);
-    const bool hasB = t < T::NHB;
-    const bool ringRow = t < T::BX;                  // phase B ring: row -1 (else column -1)
-    const int hbx = ringRow ? t : -1, hby = ringRow ? -1 : t - T::BX;
-    // measurement rings: forward link phases (row BY for Y_x/Y_z, column BX for Y_y/Y_z)
+    // phase B ring (backward plaquettes: row -1 over x in [0, BX), column -1 over y in
+    // [0, BY)) and the measurement's forward ring (Y_x/Y_z on row BY, Y_y/Y_z on
+    // column BX): each ring site goes to the thread that loaded it in phase A
+    const bool ringRow = t >= 1 && t <= T::BX;
+    const bool hasB = ringRow || (t >= 2 * T::RX && t < 2 * T::RX + BY);
+    const int hbx = ringRow ? t - 1 : -1, hby = ringRow ? -1 : t - 2 * T::RX;
+    const bool yRow = t >= T::RX + 1 && t <= T::RX + T::BX;
+    const bool hasY = yRow || (t >= 2 * T::RX + BY && t < 2 * T::RX + 2 * BY);
+    const int hyx = yRow ? t - T::RX - 1 : T::BX, hyy = yRow ? BY : t - 2 * T::RX - BY;
     // and the old E of the backward ring for the Gauss residual
-    const int hyx = ringRow ? t : T::BX, hyy = ringRow ? BY : t - T::BX;
     uint32_t hyoff = 0, hboff = 0;
-    if (MEASURE && hasB) {
-        hyoff = (uint32_t)wrapN(x0 + hyx, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hyy, N);
-        hboff = (uint32_t)wrapN(x0 + hbx, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hby, N);
-    }
+    if (MEASURE && hasY) hyoff = (uint32_t)wrapN(x0 + hyx, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hyy, N);
+    if (MEASURE && hasB) hboff = (uint32_t)wrapN(x0 + hbx, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hby, N);
     const uint32_t cxpoff = (uint32_t)wrapN(cx + 1, N) + (uint32_t)N * (uint32_t)cy;
     const uint32_t cypoff = (uint32_t)cx + (uint32_t)N * (uint32_t)wrapN(cy + 1, N);
 
@@ -143,12 +150,22 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
 
     AccT<R> acc;
     if (MEASURE) acc_zero(acc);
+    __syncthreads();   // the prologue's plane, read at neighbours in the first phase B
 
-    int b = 0;   // plane buffer holding plane zz
-    for (int zz = z0 - 1; zz < zend; ++zz) {
+    int b = 0;    // plane buffer holding plane zz
+    int pb = 0;   // buffer of the phase-B arrays of plane zz
+    for (int zz = z0 - 1; zz < zend; ++zz, pb ^= 1) {
         const int bn = b == 2 ? 0 : b + 1;   // third buffer: see the barrier note at the top
         typename T::Plane &pc = S.pl[b];
         typename T::Plane &pn = S.pl[bn];
+        R(&Sxy)[T::NS] = S.sxy[pb];
+        R(&Sxz)[T::NS] = S.sxz[pb];
+        R(&Syz)[T::NS] = S.syz[pb];
+        int(&Syx)[T::NYW] = S.yx[pb];
+        int(&Syy)[T::NYW] = S.yy[pb];
+        int(&Syzw)[T::NYW] = S.yz[pb];
+        R(&Sex)[T::NS] = S.ex[pb];
+        R(&Sey)[T::NS] = S.ey[pb];
         const uint32_t oc = (uint32_t)zc * NN, o1 = (uint32_t)z1 * NN, o2 = (uint32_t)z2 * NN;
         // ---- A: link phases and phi of plane zz+1
         phaseA(rc, T::r(tx, ty), pn);
@@ -164,7 +181,6 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
             eRing = eRingNext;
             if (gauss && hasB && zz + 1 < zend) eRingNext = P.in(ringRow ? FEY : FEX, o1 + hboff);
         }
-        __syncthreads();
 
         // ---- B: plaquettes of plane zz (tile + backward ring)
         const int r0 = T::r(tx, ty), rxp = T::r(tx + 1, ty), ryp = T::r(tx, ty + 1);
@@ -174,48 +190,48 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         const V2 Qyz = plaquette(vy0, vz0, pc.vz[ryp], pn.vy[r0]);
         {
             const int qi0 = T::q(tx, ty);
-            S.sxy[qi0] = Qxy.y;
-            S.sxz[qi0] = Qxz.y;
-            S.syz[qi0] = Qyz.y;
+            Sxy[qi0] = Qxy.y;
+            Sxz[qi0] = Qxz.y;
+            Syz[qi0] = Qyz.y;
         }
         if (hasB) {
             const int rb = T::r(hbx, hby), rbx = T::r(hbx + 1, hby), rby = T::r(hbx, hby + 1);
             const V2 bx = pc.vx[rb], by = pc.vy[rb], bz = pc.vz[rb];
             const int qh = T::q(hbx, hby);
-            S.sxy[qh] = plaquette(bx, by, pc.vy[rbx], pc.vx[rby]).y;
-            if (ringRow) S.syz[qh] = plaquette(by, bz, pc.vz[rby], pn.vy[rb]).y;
-            else S.sxz[qh] = plaquette(bx, bz, pc.vz[rbx], pn.vx[rb]).y;
+            Sxy[qh] = plaquette(bx, by, pc.vy[rbx], pc.vx[rby]).y;
+            if (ringRow) Syz[qh] = plaquette(by, bz, pc.vz[rby], pn.vy[rb]).y;
+            else Sxz[qh] = plaquette(bx, bz, pc.vz[rbx], pn.vx[rb]).y;
         }
         if (MEASURE && zz >= z0) {
             // link phases Y_i of plane zz on the tile (Y_x, Y_y carried from the
             // previous plane) and on its forward ring; old E of the backward ring
             const int wi = T::w(tx, ty);
             const V2 p0 = pc.ph[r0], pz = pn.ph[r0];
-            S.yx[wi] = YxCar;
-            S.yy[wi] = YyCar;
+            Syx[wi] = YxCar;
+            Syy[wi] = YyCar;
             const R tz0 = thz;
-            S.yz[wi] = link_phase_v(p0.x, p0.y, pz.x, pz.y, vz0.x, vz0.y, [&] { return tz0; });
+            Syzw[wi] = link_phase_v(p0.x, p0.y, pz.x, pz.y, vz0.x, vz0.y, [&] { return tz0; });
             if (gauss) {
-                S.ex[T::q(tx, ty)] = pe_cur.ex;
-                S.ey[T::q(tx, ty)] = pe_cur.ey;
+                Sex[T::q(tx, ty)] = pe_cur.ex;
+                Sey[T::q(tx, ty)] = pe_cur.ey;
             }
-            if (hasB) {
+            if (hasY) {
                 const int rh0 = T::r(hyx, hyy), wh = T::w(hyx, hyy);
                 const uint32_t ho = oc + hyoff;
                 const V2 hp = pc.ph[rh0];
-                if (ringRow) {   // row BY: Y_x
+                if (yRow) {   // row BY: Y_x
                     const V2 q = pc.ph[T::r(hyx + 1, hyy)], v = pc.vx[rh0];
-                    S.yx[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTX, ho); });
-                } else {         // column BX: Y_y
+                    Syx[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTX, ho); });
+                } else {      // column BX: Y_y
                     const V2 q = pc.ph[T::r(hyx, hyy + 1)], v = pc.vy[rh0];
-                    S.yy[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTY, ho); });
+                    Syy[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTY, ho); });
                 }
                 const V2 q = pn.ph[rh0], v = pc.vz[rh0];
-                S.yz[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTZ, ho); });
-                if (gauss) {
-                    if (ringRow) S.ey[T::q(hbx, hby)] = eRing;
-                    else S.ex[T::q(hbx, hby)] = eRing;
-                }
+                Syzw[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTZ, ho); });
+            }
+            if (gauss && hasB) {
+                if (ringRow) Sey[T::q(hbx, hby)] = eRing;
+                else Sex[T::q(hbx, hby)] = eRing;
             }
         }
         __syncthreads();
@@ -260,9 +276,9 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
             const R jy = p0.x * hy.y - p0.y * hy.x;
             const R jz = p0.x * hz.y - p0.y * hz.x;
             const R sxy = Qxy.y, sxz = Qxz.y, syz = Qyz.y;
-            const R cxv = -(sxy - S.sxy[T::q(tx, ty - 1)]) - (sxz - sxzPrev);
-            const R cyv = (sxy - S.sxy[T::q(tx - 1, ty)]) - (syz - syzPrev);
-            const R czv = (sxz - S.sxz[T::q(tx - 1, ty)]) + (syz - S.syz[T::q(tx, ty - 1)]);
+            const R cxv = -(sxy - Sxy[T::q(tx, ty - 1)]) - (sxz - sxzPrev);
+            const R cyv = (sxy - Sxy[T::q(tx - 1, ty)]) - (syz - syzPrev);
+            const R czv = (sxz - Sxz[T::q(tx - 1, ty)]) + (syz - Syz[T::q(tx, ty - 1)]);
             R enx, eny, enz, enxl = 0, enyl = 0, enzl = 0;
             if constexpr (COMP) {
                 comp_update(k.ce, pe_cur.ex, pe_cur.exl, k.ke_curl * cxv + k.ke_cur * jx, enx, enxl);
@@ -298,7 +314,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
                 const R L = rn_sub(rn_add(rn_sub(rn_sub(K, G), V), El), B);
                 const R rho = rn_add(rn_add(rn_add(rn_add(K, G), V), El), B);
                 const R pres = rn_add(rn_sub(rn_sub(K, rn_mul(G, third)), V), rn_mul(rn_add(El, B), third));
-                const R g = gauss ? gauss_site(pe_cur.ex, S.ex[T::q(tx - 1, ty)], pe_cur.ey, S.ey[T::q(tx, ty - 1)],
+                const R g = gauss ? gauss_site(pe_cur.ex, Sex[T::q(tx - 1, ty)], pe_cur.ey, Sey[T::q(tx, ty - 1)],
                                                pe_cur.ez, ezPrev, k.inv_dx, k.m_gauss, p0.x, p0.y, pe_cur.qr,
                                                pe_cur.qi)
                                   : R(0);
@@ -318,7 +334,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
 
                 // plaquette windings with lower corner x
                 const int wi = T::w(tx, ty);
-                const int Yx = YxCar, Yy = YyCar, Yz = S.yz[wi];
+                const int Yx = YxCar, Yy = YyCar, Yz = Syzw[wi];
                 const R tnx = nthx, tny = nthy;
                 const R t0x = thx, t0y = thy, t0z = thz;
                 const int wxy = wrap_from_q(Qxy.x, Qxy.y, [&](R &a, R &bb, R &c, R &d) {
@@ -327,9 +343,9 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
                     a = t0x; bb = P.in(FTZ, oc + cxpoff); c = tnx; d = t0z; });
                 const int wyz = wrap_from_q(Qyz.x, Qyz.y, [&](R &a, R &bb, R &c, R &d) {
                     a = t0y; bb = P.in(FTZ, oc + cypoff); c = tny; d = t0z; });
-                const int nxy = winding(Yx, S.yy[T::w(tx + 1, ty)], S.yx[T::w(tx, ty + 1)], Yy, wxy);
-                const int nxz = winding(Yx, S.yz[T::w(tx + 1, ty)], YxNext, Yz, wxz);
-                const int nyz = winding(Yy, S.yz[T::w(tx, ty + 1)], YyNext, Yz, wyz);
+                const int nxy = winding(Yx, Syy[T::w(tx + 1, ty)], Syx[T::w(tx, ty + 1)], Yy, wxy);
+                const int nxz = winding(Yx, Syzw[T::w(tx + 1, ty)], YxNext, Yz, wxz);
+                const int nyz = winding(Yy, Syzw[T::w(tx, ty + 1)], YyNext, Yz, wyz);
                 acc.wind += abs(nxy) + abs(nxz) + abs(nyz);
             }
 
@@ -529,15 +545,27 @@ struct Tile2 {
     static constexpr int RX = BX + 2;                                // ring sites per row: x in [-1, BX]
     static constexpr int RXP = BX + 4, RY = BY + 2, NR = RXP * RY;   // x in [-2, BX+1] (-2, BX+1: padding)
     static constexpr int SXP = BX + 2, NS = SXP * (BY + 1);          // plaquettes: x in [-2, BX), y in [-1, BY)
-    static constexpr int NHA = 2 * RX + 2 * BY, NHB = BX + BY;
-    static_assert(NHA <= NT && NHB <= NT, "ring items must fit one pass of the CTA");
+    static constexpr int NHA = 2 * RX + 2 * BY;
+    static_assert(NHA <= NT, "ring items must fit one pass of the CTA");
     struct Plane {
         float2 vx[NR], vy[NR], vz[NR], ph[NR];
     };
+    // plaquette sines: written in phase B, read in phase C, two buffers by the
+    // parity of the plane
+    struct Sines {
+        alignas(16) float sxy[NS];
+        alignas(16) float sxz[NS];
+        alignas(16) float syz[NS];
+    };
     struct Smem {
         Plane pl[3];
-        float sxy[NS], sxz[NS], syz[NS];
+        Sines sn[2];
     };
+    // the pair reads and writes link phases and phi as float4, plaquette sines as
+    // float2, at even indices
+    static_assert(sizeof(Plane) % 16 == 0 && (NR * sizeof(float2)) % 16 == 0 && SXP % 2 == 0 &&
+                      sizeof(Sines) % 16 == 0,
+                  "pair accesses must stay aligned");
     // even for even ex: the pair (ex, ex+1) is one aligned float4 / float2
     static __device__ __forceinline__ int r(int ex, int ey) { return (ey + 1) * RXP + (ex + 2); }
     static __device__ __forceinline__ int q(int ex, int ey) { return (ey + 1) * SXP + (ex + 2); }
@@ -571,9 +599,11 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
         else { hax = T::BX; hay = t - 2 * T::RX - BY; }
     }
     const uint32_t haoff = (uint32_t)wrapN(x0 + hax, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hay, N);
-    const bool hasB = t < T::NHB;
-    const bool ringRow = t < T::BX;
-    const int hbx = ringRow ? t : -1, hby = ringRow ? -1 : t - T::BX;
+    // phase B ring (row -1 over x in [0, BX), column -1 over y in [0, BY)): each
+    // site goes to the thread that loaded it in phase A
+    const bool ringRow = t >= 1 && t <= T::BX;
+    const bool hasB = ringRow || (t >= 2 * T::RX && t < 2 * T::RX + BY);
+    const int hbx = ringRow ? t - 1 : -1, hby = ringRow ? -1 : t - 2 * T::RX;
 
     auto ld2 = [&](const float *p, uint32_t o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
     auto st2 = [&](float *p, uint32_t o, float a, float b) { *reinterpret_cast<float2 *>(p + o) = make_float2(a, b); };
@@ -639,11 +669,14 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
     V2 vzPrev[2] = {make_float2(1.f, 0.f), make_float2(1.f, 0.f)};
     float sxzPrev[2] = {0.f, 0.f}, syzPrev[2] = {0.f, 0.f};
 
-    int b = 0;
-    for (int zz = z0 - 1; zz < zend; ++zz) {
+    __syncthreads();   // the prologue's plane, read at neighbours in the first phase B
+
+    int b = 0, pb = 0;
+    for (int zz = z0 - 1; zz < zend; ++zz, pb ^= 1) {
         const int bn = b == 2 ? 0 : b + 1;
         typename T::Plane &pc = S.pl[b];
         typename T::Plane &pn = S.pl[bn];
+        typename T::Sines &Sn = S.sn[pb];
         const uint32_t oc = (uint32_t)zc * NN, o1 = (uint32_t)z1 * NN, o2 = (uint32_t)z2 * NN;
         // ---- A: link phases and phi of plane zz+1
         phaseA2(rc, pn);
@@ -655,7 +688,6 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
         }
         pe_cur = pe_next;
         if (zz + 1 < zend) pe_next = load_pe2(o1 + coff);
-        __syncthreads();
 
         // ---- B: plaquettes of plane zz (the pair + backward ring)
         V2 Qxy[2], Qxz[2], Qyz[2];
@@ -669,17 +701,17 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
         }
         {
             const int qi0 = T::q(ex, ty);
-            *reinterpret_cast<float2 *>(&S.sxy[qi0]) = make_float2(Qxy[0].y, Qxy[1].y);
-            *reinterpret_cast<float2 *>(&S.sxz[qi0]) = make_float2(Qxz[0].y, Qxz[1].y);
-            *reinterpret_cast<float2 *>(&S.syz[qi0]) = make_float2(Qyz[0].y, Qyz[1].y);
+            *reinterpret_cast<float2 *>(&Sn.sxy[qi0]) = make_float2(Qxy[0].y, Qxy[1].y);
+            *reinterpret_cast<float2 *>(&Sn.sxz[qi0]) = make_float2(Qxz[0].y, Qxz[1].y);
+            *reinterpret_cast<float2 *>(&Sn.syz[qi0]) = make_float2(Qyz[0].y, Qyz[1].y);
         }
         if (hasB) {
             const int rb = T::r(hbx, hby), rbx = T::r(hbx + 1, hby), rby = T::r(hbx, hby + 1);
             const V2 bx = pc.vx[rb], by = pc.vy[rb], bz = pc.vz[rb];
             const int qh = T::q(hbx, hby);
-            S.sxy[qh] = plaquette(bx, by, pc.vy[rbx], pc.vx[rby]).y;
-            if (ringRow) S.syz[qh] = plaquette(by, bz, pc.vz[rby], pn.vy[rb]).y;
-            else S.sxz[qh] = plaquette(bx, bz, pc.vz[rbx], pn.vx[rb]).y;
+            Sn.sxy[qh] = plaquette(bx, by, pc.vy[rbx], pc.vx[rby]).y;
+            if (ringRow) Sn.syz[qh] = plaquette(by, bz, pc.vz[rby], pn.vy[rb]).y;
+            else Sn.sxz[qh] = plaquette(bx, bz, pc.vz[rbx], pn.vx[rb]).y;
         }
         __syncthreads();
 
@@ -711,9 +743,9 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
                 const float jy = p0.x * hy.y - p0.y * hy.x;
                 const float jz = p0.x * hz.y - p0.y * hz.x;
                 const float sxy = Qxy[j].y, sxz = Qxz[j].y, syz = Qyz[j].y;
-                const float cxv = -(sxy - S.sxy[T::q(ex + j, ty - 1)]) - (sxz - sxzPrev[j]);
-                const float cyv = (sxy - S.sxy[T::q(ex + j - 1, ty)]) - (syz - syzPrev[j]);
-                const float czv = (sxz - S.sxz[T::q(ex + j - 1, ty)]) + (syz - S.syz[T::q(ex + j, ty - 1)]);
+                const float cxv = -(sxy - Sn.sxy[T::q(ex + j, ty - 1)]) - (sxz - sxzPrev[j]);
+                const float cyv = (sxy - Sn.sxy[T::q(ex + j - 1, ty)]) - (syz - syzPrev[j]);
+                const float czv = (sxz - Sn.sxz[T::q(ex + j - 1, ty)]) + (syz - Sn.syz[T::q(ex + j, ty - 1)]);
                 en[j][0] = k.ce * e0x + k.ke_curl * cxv + k.ke_cur * jx;
                 en[j][1] = k.ce * e0y + k.ke_curl * cyv + k.ke_cur * jy;
                 en[j][2] = k.ce * e0z + k.ke_curl * czv + k.ke_cur * jz;
