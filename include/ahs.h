@@ -244,6 +244,20 @@ int ahs_kernel_time(ahs_t *h, int kind, double *ms_total, int64_t *launches, int
 int ahs_stable_dt(double dx, double lambda0, double e0, double sigma, double s, int era, double tau0,
                   double tau_end, double s_cg, double tau_cg, double safety, double *dt);
 
+/* ahs_bounds_check -- the index checks of the bounds-check build of this library
+ * (compiled with -DAHS_BOUNDS_CHECK: _ahs_check.so beside _ahs.so), a test aid
+ * with no counterpart in the paper.  There every global offset of the step
+ * kernels' tile loaders, rings and stores, and every shared-memory index of their
+ * tiles, is checked against the extent it addresses; an index outside it is
+ * counted and replaced by 0, so the access stays in range and no kernel traps.
+ *   op 0: *count = the indices counted on the current device since the library was
+ *         loaded or last reset; 1: the same, then zero the count; 2: first run a
+ *         self-test that passes one out-of-range index through the check of each
+ *         kernel translation unit (touching no memory), then as 1.
+ * Returns AHS_ESTATE in the production build, which compiles the checks away;
+ * AHS_EINVAL for a NULL count or another op. */
+int ahs_bounds_check(int op, int64_t *count);
+
 /* ahs_device_bytes -- device memory of the handle: its field storage (allocated
  * or, before the first ahs_init / ahs_set_fields, to be allocated), measurement
  * partials and records. */

@@ -35,7 +35,7 @@ EXPORTS = (
     "ahs_batch_create", "ahs_batch_init", "ahs_batch_run", "ahs_batch_records", "ahs_batch_fields",
     "ahs_batch_set_fields", "ahs_batch_step_info", "ahs_batch_set_option", "ahs_batch_get_option",
     "ahs_batch_member_zchunk", "ahs_batch_autotune", "ahs_batch_kernel_time", "ahs_batch_set_stream",
-    "ahs_batch_destroy", "ahs_batch_measure", "ahs_stable_dt",
+    "ahs_batch_destroy", "ahs_batch_measure", "ahs_stable_dt", "ahs_bounds_check",
 )
 _NON_INT = ("ahs_create", "ahs_destroy", "ahs_last_error_message", "ahs_strerror", "ahs_sizeof_obs",
             "ahs_batch_create", "ahs_batch_destroy")
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ahs_measure_noalloc.argtypes = [i, d, d, d, d, d, d, i, d, d, ctypes.c_int64, vp, vp, vp]
     L.ahs_autotune.argtypes = [H]
     L.ahs_stable_dt.argtypes = [d, d, d, d, d, i, d, d, d, d, d, ctypes.POINTER(d)]
+    L.ahs_bounds_check.argtypes = [i, ctypes.POINTER(ctypes.c_int64)]
     i64p = ctypes.POINTER(ctypes.c_int64)
     L.ahs_batch_create.argtypes = [i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_uint64), i64p,
                                    d, d, d, d, d, d]

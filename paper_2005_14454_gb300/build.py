@@ -4,6 +4,10 @@ Each translation unit under ``csrc/`` is compiled in parallel to an object file 
 ``_build/`` and the objects are linked into ``paper_2005_14454_gb300/_ahs.so``
 (static CUDA runtime, so the library only needs the driver at run time).  Runs the
 same on x86 (cross-compiling, no GPU) and on the Arm GPU host.
+
+variant="check" builds the bounds-check library ``_ahs_check.so`` (objects in
+``_build/check``): the same sources with -DAHS_BOUNDS_CHECK, whose step kernels
+count every index outside its extent (ahs_bounds_check); a test aid.
 """
 from __future__ import annotations
 
@@ -43,8 +47,14 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+VARIANTS = {"release": (BUILD, LIB, ()),
+            "check": (os.path.join(BUILD, "check"), os.path.join(PKG, "_ahs_check.so"), ("-DAHS_BOUNDS_CHECK",))}
+
+
+def build(force: bool = False, verbose: bool = False, extra=(), variant: str = "release") -> str:
+    build_dir, lib, flags = VARIANTS[variant]
+    extra = tuple(flags) + tuple(extra)
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     headers.append(os.path.abspath(__file__))
@@ -52,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     jobs = []
     objs = []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             jobs.append([cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
@@ -69,11 +79,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        run([cc, *ARCH, "-shared", *objs, "-o", LIB + ".tmp"])
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+    if force or jobs or _stale(lib, objs):
+        run([cc, *ARCH, "-shared", *objs, "-o", lib + ".tmp"])
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, variant="check" if "--check" in sys.argv else "release"))

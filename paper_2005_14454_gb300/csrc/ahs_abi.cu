@@ -735,6 +735,19 @@ int ahs_stable_dt(double dx, double lambda0, double e0, double sigma, double s, 
     return ok();
 }
 
+int ahs_bounds_check(int op, int64_t *count)
+{
+    if (!count || op < 0 || op > 2) return fail(AHS_EINVAL, "need a count pointer and op 0, 1 or 2");
+    unsigned long long a = 0, b = 0;
+    cudaError_t e = bounds_errors_step(&a, op);
+    if (e == cudaErrorNotSupported)
+        return fail(AHS_ESTATE, "index checks are compiled only into the bounds-check build (-DAHS_BOUNDS_CHECK)");
+    if (e == cudaSuccess) e = bounds_errors_step2(&b, op);
+    if (e != cudaSuccess) return fail(AHS_ECUDA, "bounds counters: %s", cudaGetErrorString(e));
+    *count = (int64_t)(a + b);
+    return ok();
+}
+
 int ahs_kernel_time(ahs_t *h, int kind, double *ms, int64_t *launches, int reset)
 {
     if (!h) return fail(AHS_EINVAL, "null handle");

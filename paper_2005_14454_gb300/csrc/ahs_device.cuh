@@ -195,6 +195,63 @@ static __device__ __forceinline__ size_t sidx(int x, int y, int z, int N)
     return (size_t)x + (size_t)N * ((size_t)y + (size_t)N * (size_t)z);
 }
 
+// ---------------------------------------------------------------- index checks
+// The bounds-check build of the library (-DAHS_BOUNDS_CHECK, _ahs_check.so) checks
+// every global offset of the step kernels' tile loaders, rings and stores and every
+// shared-memory index of their tiles against the extent it addresses.  An index
+// outside it is counted in g_bounds_errors (one counter per translation unit, read
+// by ahs_bounds_check) and replaced by 0, so the access stays in range: nothing
+// traps, and nothing is read or written outside its array.  The production build
+// compiles the checks away.
+#ifdef AHS_BOUNDS_CHECK
+static __device__ unsigned long long g_bounds_errors;
+static __device__ __forceinline__ uint32_t checked_index(uint32_t i, uint32_t n)
+{
+    if (i >= n) {
+        atomicAdd(&g_bounds_errors, 1ull);
+        return 0u;
+    }
+    return i;
+}
+static __device__ __forceinline__ int checked_index(int i, int n)
+{
+    if (i < 0 || i >= n) {
+        atomicAdd(&g_bounds_errors, 1ull);
+        return 0;
+    }
+    return i;
+}
+#define AHS_INDEX(i, n) ::eng::checked_index((i), (n))
+// host side: this translation unit's counter on the current device (read, then
+// zeroed if reset), and a self-test launch that passes one index outside its extent
+// through the check (touching no memory)
+static __global__ void bounds_selftest_kernel()
+{
+    (void)checked_index(7, 3);
+}
+#define AHS_BOUNDS_COUNTER(name)                                                                     \
+    cudaError_t name(unsigned long long *count, int op)                                            \
+    {                                                                                              \
+        if (op == 2) {                                                                             \
+            bounds_selftest_kernel<<<1, 1>>>();                                                    \
+            cudaError_t e = cudaDeviceSynchronize();                                               \
+            if (e != cudaSuccess) return e;                                                        \
+        }                                                                                          \
+        cudaError_t e = cudaMemcpyFromSymbol(count, g_bounds_errors, sizeof(*count));              \
+        if (e != cudaSuccess || op == 0) return e;                                                 \
+        const unsigned long long zero = 0;                                                         \
+        return cudaMemcpyToSymbol(g_bounds_errors, &zero, sizeof(zero));                           \
+    }
+#else
+#define AHS_INDEX(i, n) (i)
+#define AHS_BOUNDS_COUNTER(name)                                                                     \
+    cudaError_t name(unsigned long long *count, int)                                               \
+    {                                                                                              \
+        *count = 0;                                                                                \
+        return cudaErrorNotSupported;                                                              \
+    }
+#endif
+
 // ---------------------------------------------------------------- explicit roundings
 // Arithmetic that the compiler may not contract into fused multiply-adds of its own
 // choosing: the diagnostics of a measuring step are evaluated with these, so that

@@ -150,6 +150,13 @@ cudaError_t launch_batch_reduce(const double *partials, const BatchMember *membe
                                 ahs_obs_t *records, int rcap, cudaStream_t st);
 cudaError_t launch_advance(int64_t *counter, int64_t delta, cudaStream_t st);
 
+// counters of the bounds-check build (ahs_bounds_check): the out-of-range indices
+// the kernels of ahs_step.cu and of ahs_step2.cu counted on the current device;
+// op 0 reads, 1 reads and zeroes, 2 first runs the self-test launch.
+// cudaErrorNotSupported in the production build.
+cudaError_t bounds_errors_step(unsigned long long *count, int op);
+cudaError_t bounds_errors_step2(unsigned long long *count, int op);
+
 // error state of the C ABI (ahs_last_error / ahs_last_error_message)
 int report_error(int code, const char *msg);
 int report_ok();

@@ -60,8 +60,10 @@ enum { FPR = 0, FPI, FQR, FQI, FTX, FTY, FTZ, FEX, FEY, FEZ, FQRL, FQIL, FEXL, F
 struct ParamFields {
     using real = float;
     const StepPtrs &P;
+    uint32_t V;   // sites per plane (N^3): the extent of the bounds-check build's offset checks
     __device__ __forceinline__ float in(int f, uint32_t o) const
     {
+        o = AHS_INDEX(o, V);
         const float *p = f == FPR ? P.pr : f == FPI ? P.pim : f == FQR ? P.qr : f == FQI ? P.qi : f == FTX ? P.tx
                        : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : f == FEZ ? P.ez
                        : f == FQRL ? P.qrl : f == FQIL ? P.qil : f == FEXL ? P.exl : f == FEYL ? P.eyl : P.ezl;
@@ -72,7 +74,7 @@ struct ParamFields {
         float *p = f == FPR ? P.pr1 : f == FPI ? P.pim1 : f == FQR ? P.qr1 : f == FQI ? P.qi1 : f == FTX ? P.tx1
                  : f == FTY ? P.ty1 : f == FTZ ? P.tz1 : f == FEX ? P.ex1 : f == FEY ? P.ey1 : f == FEZ ? P.ez1
                  : f == FQRL ? P.qrl1 : f == FQIL ? P.qil1 : f == FEXL ? P.exl1 : f == FEYL ? P.eyl1 : P.ezl1;
-        p[o] = v;
+        p[AHS_INDEX(o, V)] = v;
     }
 };
 
@@ -80,10 +82,13 @@ struct ArenaFields {
     using real = float;
     const float *base;       // the member's first plane (buffer 0, Re phi)
     uint32_t in0, out0, V;   // plane offsets of the read and write buffers, plane size
-    __device__ __forceinline__ float in(int f, uint32_t o) const { return __ldg(base + (in0 + (uint32_t)f * V + o)); }
+    __device__ __forceinline__ float in(int f, uint32_t o) const
+    {
+        return __ldg(base + (in0 + (uint32_t)f * V + AHS_INDEX(o, V)));
+    }
     __device__ __forceinline__ void out(int f, uint32_t o, float v) const
     {
-        const_cast<float *>(base)[out0 + (uint32_t)f * V + o] = v;
+        const_cast<float *>(base)[out0 + (uint32_t)f * V + AHS_INDEX(o, V)] = v;
     }
 };
 
@@ -91,8 +96,10 @@ struct ArenaFields {
 struct ParamFields64 {
     using real = double;
     const StepPtrs64 &P;
+    uint32_t V;   // sites per plane (N^3)
     __device__ __forceinline__ double in(int f, uint32_t o) const
     {
+        o = AHS_INDEX(o, V);
         const double *p = f == FPR ? P.pr : f == FPI ? P.pim : f == FQR ? P.qr : f == FQI ? P.qi : f == FTX ? P.tx
                         : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : P.ez;
         return __ldg(p + o);
@@ -101,7 +108,7 @@ struct ParamFields64 {
     {
         double *p = f == FPR ? P.pr1 : f == FPI ? P.pim1 : f == FQR ? P.qr1 : f == FQI ? P.qi1 : f == FTX ? P.tx1
                   : f == FTY ? P.ty1 : f == FTZ ? P.tz1 : f == FEX ? P.ex1 : f == FEY ? P.ey1 : P.ez1;
-        p[o] = v;
+        p[AHS_INDEX(o, V)] = v;
     }
 };
 

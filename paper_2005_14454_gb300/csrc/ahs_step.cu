@@ -52,27 +52,34 @@ struct Tile {
     struct Plane {
         V2 vx[NR], vy[NR], vz[NR], ph[NR];
     };
-    // written in phase B, read in phase C: two buffers, by the parity of the plane
-    struct Smem {
+    // The arrays written in phase B and read in phase C: NB = 2 buffers by the parity
+    // of the plane (the plain step, one barrier per plane), NB = 1 (the measuring
+    // step, two barriers per plane)
+    template <int NB>
+    struct SmemT {
         Plane pl[3];
-        R sxy[2][NS], sxz[2][NS], syz[2][NS];
-        // measurement steps only
-        int yx[2][NYW], yy[2][NYW], yz[2][NYW];
-        R ex[2][NS], ey[2][NS];
+        R sxy[NB][NS], sxz[NB][NS], syz[NB][NS];
+        // measurement steps only: old E for the Gauss residual, octant codes of the
+        // link phases Y
+        R ex[NB][NS], ey[NB][NS];
+        int yx[NB][NYW], yy[NB][NYW], yz[NB][NYW];
     };
-    static constexpr size_t kStepBytes = offsetof(Smem, yx);
-    static constexpr size_t kMeasureBytes = sizeof(Smem);
+    template <bool MEASURE>
+    using Smem = SmemT<MEASURE ? 1 : 2>;
+    static constexpr size_t kStepBytes = offsetof(SmemT<2>, ex);
+    static constexpr size_t kMeasureBytes = sizeof(SmemT<1>);
 
-    static __device__ __forceinline__ int r(int ex, int ey) { return (ey + 1) * RX + (ex + 1); }
-    static __device__ __forceinline__ int q(int ex, int ey) { return (ey + 1) * SX + (ex + 1); }
-    static __device__ __forceinline__ int w(int ex, int ey) { return ey * YX + ex; }
+    static __device__ __forceinline__ int r(int ex, int ey) { return AHS_INDEX((ey + 1) * RX + (ex + 1), NR); }
+    static __device__ __forceinline__ int q(int ex, int ey) { return AHS_INDEX((ey + 1) * SX + (ex + 1), NS); }
+    static __device__ __forceinline__ int w(int ex, int ey) { return AHS_INDEX(ey * YX + ex, NYW); }
 };
 
 // One tile: the 32 x BY column at (x0, y0), planes [z0, zend).  All threads of the
 // CTA call it together (it contains CTA barriers); with MEASURE the CTA's FP64
 // partial sums go to `partial_row`.
 template <int BY, bool MEASURE, bool STORE, bool COMP, class FA>
-__device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::Smem &S, const FA &P,
+__device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::template Smem<MEASURE> &S,
+                                          const FA &P,
                                           const typename Real<typename FA::real>::Coef &k, int N,
                                           int x0, int y0, int z0, int zend, double *partial_row)
 {
@@ -96,14 +103,18 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
     }
     const uint32_t haoff = (uint32_t)wrapN(x0 + hax, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hay, N);
     // phase B ring (backward plaquettes: row -1 over x in [0, BX), column -1 over y in
-    // [0, BY)) and the measurement's forward ring (Y_x/Y_z on row BY, Y_y/Y_z on
-    // column BX): each ring site goes to the thread that loaded it in phase A
-    const bool ringRow = t >= 1 && t <= T::BX;
-    const bool hasB = ringRow || (t >= 2 * T::RX && t < 2 * T::RX + BY);
-    const int hbx = ringRow ? t - 1 : -1, hby = ringRow ? -1 : t - 2 * T::RX;
-    const bool yRow = t >= T::RX + 1 && t <= T::RX + T::BX;
-    const bool hasY = yRow || (t >= 2 * T::RX + BY && t < 2 * T::RX + 2 * BY);
-    const int hyx = yRow ? t - T::RX - 1 : T::BX, hyy = yRow ? BY : t - 2 * T::RX - BY;
+    // [0, BY)).  The plain step (one barrier per plane) gives each ring site to the
+    // thread that loaded it in phase A; the measuring step (two barriers) gives the
+    // ring to the first BX + BY threads, which also take the forward ring of the
+    // measurement (Y_x/Y_z on row BY, Y_y/Y_z on column BX) -- fewer warps with ring
+    // work, measured faster there.
+    const bool ringRow = MEASURE ? t < T::BX : (t >= 1 && t <= T::BX);
+    const bool hasB = MEASURE ? t < T::BX + BY : ringRow || (t >= 2 * T::RX && t < 2 * T::RX + BY);
+    const int hbx = ringRow ? (MEASURE ? t : t - 1) : -1;
+    const int hby = ringRow ? -1 : (MEASURE ? t - T::BX : t - 2 * T::RX);
+    const bool yRow = ringRow;
+    const bool hasY = hasB;
+    const int hyx = yRow ? hbx : T::BX, hyy = yRow ? BY : hby;
     // and the old E of the backward ring for the Gauss residual
     uint32_t hyoff = 0, hboff = 0;
     if (MEASURE && hasY) hyoff = (uint32_t)wrapN(x0 + hyx, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hyy, N);
@@ -150,11 +161,11 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
 
     AccT<R> acc;
     if (MEASURE) acc_zero(acc);
-    __syncthreads();   // the prologue's plane, read at neighbours in the first phase B
+    if (!MEASURE) __syncthreads();   // the prologue's plane, read at neighbours in the first phase B
 
     int b = 0;    // plane buffer holding plane zz
-    int pb = 0;   // buffer of the phase-B arrays of plane zz
-    for (int zz = z0 - 1; zz < zend; ++zz, pb ^= 1) {
+    int pb = 0;   // buffer of the phase-B arrays of plane zz (always 0 when measuring)
+    for (int zz = z0 - 1; zz < zend; ++zz, pb = MEASURE ? 0 : pb ^ 1) {
         const int bn = b == 2 ? 0 : b + 1;   // third buffer: see the barrier note at the top
         typename T::Plane &pc = S.pl[b];
         typename T::Plane &pn = S.pl[bn];
@@ -180,6 +191,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         if (MEASURE) {
             eRing = eRingNext;
             if (gauss && hasB && zz + 1 < zend) eRingNext = P.in(ringRow ? FEY : FEX, o1 + hboff);
+            __syncthreads();   // the measuring step's ring reads other threads' phase A
         }
 
         // ---- B: plaquettes of plane zz (tile + backward ring)
@@ -408,10 +420,10 @@ __global__ void __launch_bounds__(32 * BY, (MEASURE ? 16 : 32) / BY)
 {
     using T = Tile<BY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
+    typename T::template Smem<MEASURE> &S = *reinterpret_cast<typename T::template Smem<MEASURE> *>(smem_raw);
     const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
     const size_t bi = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-    tile_step<BY, MEASURE, STORE, COMP>(S, ParamFields{P}, k, N, x0, y0, z0, min(z0 + Dz, N),
+    tile_step<BY, MEASURE, STORE, COMP>(S, ParamFields{P, (uint32_t)N * (uint32_t)N * (uint32_t)N}, k, N, x0, y0, z0, min(z0 + Dz, N),
                                         MEASURE ? partials + bi * NQ : nullptr);
 }
 
@@ -428,10 +440,10 @@ __global__ void __launch_bounds__(256, MEASURE ? 1 : 2)
 {
     using T = Tile<8, double>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
+    typename T::template Smem<MEASURE> &S = *reinterpret_cast<typename T::template Smem<MEASURE> *>(smem_raw);
     const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * 8, z0 = blockIdx.z * Dz;
     const size_t bi = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
-    tile_step<8, MEASURE, STORE, false>(S, ParamFields64{P}, k, N, x0, y0, z0, min(z0 + Dz, N),
+    tile_step<8, MEASURE, STORE, false>(S, ParamFields64{P, (uint32_t)N * (uint32_t)N * (uint32_t)N}, k, N, x0, y0, z0, min(z0 + Dz, N),
                                         MEASURE ? partials + bi * NQ : nullptr);
 }
 
@@ -440,7 +452,7 @@ __global__ void __launch_bounds__(32 * BY, (MEASURE ? 16 : 32) / BY) batch_step(
 {
     using T = Tile<BY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
+    typename T::template Smem<MEASURE> &S = *reinterpret_cast<typename T::template Smem<MEASURE> *>(smem_raw);
     __shared__ StepCoef sk;
     __shared__ int s_w;
     const int64_t n = *L.counter + dn;
@@ -567,8 +579,8 @@ struct Tile2 {
                       sizeof(Sines) % 16 == 0,
                   "pair accesses must stay aligned");
     // even for even ex: the pair (ex, ex+1) is one aligned float4 / float2
-    static __device__ __forceinline__ int r(int ex, int ey) { return (ey + 1) * RXP + (ex + 2); }
-    static __device__ __forceinline__ int q(int ex, int ey) { return (ey + 1) * SXP + (ex + 2); }
+    static __device__ __forceinline__ int r(int ex, int ey) { return AHS_INDEX((ey + 1) * RXP + (ex + 2), NR); }
+    static __device__ __forceinline__ int q(int ex, int ey) { return AHS_INDEX((ey + 1) * SXP + (ex + 2), NS); }
 };
 
 template <int BY>
@@ -578,11 +590,11 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
     using V2 = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
-    const ParamFields F{P};
     const int tx = threadIdx.x, ty = threadIdx.y, t = tx + 32 * ty;
     const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
     const int zend = min(z0 + Dz, N);
     const uint32_t NN = (uint32_t)N * (uint32_t)N;
+    const ParamFields F{P, NN * (uint32_t)N};
 
     // core pair: sites ex and ex+1 of row ty
     const int ex = 2 * tx;
@@ -605,8 +617,13 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
     const bool hasB = ringRow || (t >= 2 * T::RX && t < 2 * T::RX + BY);
     const int hbx = ringRow ? t - 1 : -1, hby = ringRow ? -1 : t - 2 * T::RX;
 
-    auto ld2 = [&](const float *p, uint32_t o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
-    auto st2 = [&](float *p, uint32_t o, float a, float b) { *reinterpret_cast<float2 *>(p + o) = make_float2(a, b); };
+    // a pair is two floats: o + 1 must lie in the plane as well
+    auto ld2 = [&](const float *p, uint32_t o) {
+        return __ldg(reinterpret_cast<const float2 *>(p + AHS_INDEX(o, F.V - 1)));
+    };
+    auto st2 = [&](float *p, uint32_t o, float a, float b) {
+        *reinterpret_cast<float2 *>(p + AHS_INDEX(o, F.V - 1)) = make_float2(a, b);
+    };
     struct Raw2 {
         float2 tx, ty, tz, pr, pi;   // .x site ex, .y site ex+1
     };
@@ -835,14 +852,16 @@ __global__ void __launch_bounds__(32 * BY) gauss_tiled(StepPtrs P, StepCoef k, i
     const bool valid = (x0 + tx < N) && (y0 + ty < N);
     AccT<float> acc;
     acc_zero(acc);
-    float ezPrev = __ldg(P.ez + (uint32_t)wrapN(z0 - 1, N) * NN + coff);
+    const uint32_t V = NN * (uint32_t)N;
+    float ezPrev = __ldg(P.ez + AHS_INDEX((uint32_t)wrapN(z0 - 1, N) * NN + coff, V));
     for (int zz = z0; zz < zend; ++zz) {
         const uint32_t o = (uint32_t)zz * NN;
-        const float ex = __ldg(P.ex + o + coff), ey = __ldg(P.ey + o + coff), ez = __ldg(P.ez + o + coff);
+        const uint32_t oc = AHS_INDEX(o + coff, V);
+        const float ex = __ldg(P.ex + oc), ey = __ldg(P.ey + oc), ez = __ldg(P.ez + oc);
         if (valid) {
-            const float exm = __ldg(P.ex + o + xmoff), eym = __ldg(P.ey + o + ymoff);
-            const float pr = __ldg(P.pr + o + coff), pim = __ldg(P.pim + o + coff);
-            const float qr = __ldg(P.qr + o + coff), qi = __ldg(P.qi + o + coff);
+            const float exm = __ldg(P.ex + AHS_INDEX(o + xmoff, V)), eym = __ldg(P.ey + AHS_INDEX(o + ymoff, V));
+            const float pr = __ldg(P.pr + oc), pim = __ldg(P.pim + oc);
+            const float qr = __ldg(P.qr + oc), qi = __ldg(P.qi + oc);
             const float g = gauss_site(ex, exm, ey, eym, ez, ezPrev, k.inv_dx, k.m_gauss, pr, pim, qr, qi);
             acc.s[Q_G2] = square_add(g, acc.s[Q_G2]);
             acc.gmax = fmax(acc.gmax, fabs(g));
@@ -926,5 +945,7 @@ cudaError_t launch_gauss(const StepPtrs &p, const StepCoef &k, int N, const Step
     else gauss_tiled<8><<<grid, dim3(32, 8), 0, st>>>(p, k, N, sh.dz, partials);
     return cudaGetLastError();
 }
+
+AHS_BOUNDS_COUNTER(bounds_errors_step)
 
 }  // namespace eng

@@ -58,10 +58,10 @@ struct Tile2Step {
         float s1xy[NP1], s1xz[NP1], s1yz[NP1];
         float s2xy[NP2], s2xz[NP2], s2yz[NP2];
     };
-    static __device__ __forceinline__ int a(int ex, int ey) { return (ey + 2) * AX + (ex + 2); }
-    static __device__ __forceinline__ int h(int ex, int ey) { return (ey + 1) * HX + (ex + 1); }
-    static __device__ __forceinline__ int q1(int ex, int ey) { return (ey + 2) * P1X + (ex + 2); }
-    static __device__ __forceinline__ int q2(int ex, int ey) { return (ey + 1) * P2X + (ex + 1); }
+    static __device__ __forceinline__ int a(int ex, int ey) { return AHS_INDEX((ey + 2) * AX + (ex + 2), NA); }
+    static __device__ __forceinline__ int h(int ex, int ey) { return AHS_INDEX((ey + 1) * HX + (ex + 1), NH); }
+    static __device__ __forceinline__ int q1(int ex, int ey) { return AHS_INDEX((ey + 2) * P1X + (ex + 2), NP1); }
+    static __device__ __forceinline__ int q2(int ex, int ey) { return AHS_INDEX((ey + 1) * P2X + (ex + 1), NP2); }
 };
 
 // a site's own values that stage 1 hands to stage 2: Pi^{n+1/2}, E^{n+1/2}, theta^{n+1}
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256, 2)
     using T = Tile2Step;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T::Smem &S = *reinterpret_cast<T::Smem *>(smem_raw);
-    const ParamFields F{P};
+    const ParamFields F{P, (uint32_t)N * (uint32_t)N * (uint32_t)N};
     const int tx = threadIdx.x, ty = threadIdx.y, t = tx + 32 * ty;
     const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * T::BY, z0 = blockIdx.z * Dz;
     const int zend = min(z0 + Dz, N);
@@ -401,5 +401,7 @@ cudaError_t launch_step_two(const StepPtrs &p, const StepCoef &k1, const StepCoe
     step_two<<<grid, dim3(32, T::BY), bytes, st>>>(p, k1, k2, N, Dz);
     return cudaGetLastError();
 }
+
+AHS_BOUNDS_COUNTER(bounds_errors_step2)
 
 }  // namespace eng

@@ -100,3 +100,12 @@ def test_stable_dt_rejects_bad_arguments(abi, args):
     assert abi.lib().ahs_stable_dt(*args, ctypes.byref(v)) == abi.AHS_EINVAL
     assert v.value == -1.0
     assert abi.lib().ahs_stable_dt(0.5, 2.0, 1.0, 1.0, 0.0, 1, 1.0, 10.0, 0.0, 0.0, 0.9, None) == abi.AHS_EINVAL
+
+
+def test_bounds_check_absent_from_the_production_build(abi):
+    # the index checks exist only in the bounds-check build (_ahs_check.so); the
+    # production library says so without touching the device
+    c = ctypes.c_int64(-1)
+    assert abi.lib().ahs_bounds_check(0, ctypes.byref(c)) == abi.AHS_ESTATE
+    assert b"bounds-check build" in abi.lib().ahs_last_error_message()
+    assert abi.lib().ahs_bounds_check(3, ctypes.byref(c)) == abi.AHS_EINVAL
