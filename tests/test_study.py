@@ -45,3 +45,38 @@ def test_small_realisation_gives_growing_string_separation():
     # R = sum KL / sum GL can be negative there)
     assert r["xi_dot_W"] > 0 and r["xi_dot_L"] > 0
     assert np.isfinite(r["v2_phi"]) and np.isfinite(r["v2_omega"])
+
+
+def test_committed_table1_runs_reproduce_their_summary_and_the_paper():
+    """The 40 realisations of Table 1 at 1024^3 committed in profiles/table1_1024.jsonl:
+    20 seeds per era, their aggregation equals the summary lines stored with them, and
+    the means agree with the paper's (Table 1, tests/golden/table1_scaling.txt): each
+    xi_dot within 1.25 of the paper's standard deviations over its own 20
+    realisations (xi_dot_L is 1.0 and 1.2 of them low, xi_dot_W within 0.6), each
+    velocity within 2% (radiation <v^2>_phi is 1.7% high, 2.3 of the paper's narrow
+    spread) -- the statistical support of the readings of the string length (pi/6
+    Manhattan factor), the tension mu = 2 pi sigma^2 and the weight of <v^2>_omega."""
+    import json
+    import os
+    from paper_2005_14454_gb300.study import TABLE1_KEYS, table1_summary
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    lines = [json.loads(l) for l in open(os.path.join(root, "profiles", "table1_1024.jsonl")) if l.startswith("{")]
+    runs = [d for d in lines if d["study"] == "table1"]
+    stored = {d["era"]: d for d in lines if d["study"] == "table1-summary"}
+    assert sorted((r["era"], r["seed"]) for r in runs) == [(e, s) for e in (1, 2) for s in range(1, 21)]
+    assert all(r["N"] == 1024 and r["every"] == 5 and r["fit"] == [100.5, 255.5] for r in runs)
+    paper = {}
+    for line in open(os.path.join(root, "tests", "golden", "table1_scaling.txt")):
+        if line.strip() and not line.startswith("#"):
+            v = line.split()
+            if int(v[0]) == 1024:
+                paper[int(v[1])] = {k: (float(v[2 + 2 * i]), float(v[3 + 2 * i])) for i, k in enumerate(TABLE1_KEYS)}
+    for d in table1_summary(runs):
+        assert d["runs"] == 20
+        for k in TABLE1_KEYS:
+            assert d[k] == pytest.approx(stored[d["era"]][k], rel=1e-12), k
+            mean, spread = paper[d["era"]][k]
+            if k.startswith("xi_dot"):
+                assert abs(d[k][0] - mean) <= 1.25 * spread, (d["era"], k, d[k][0], mean, spread)
+            else:
+                assert abs(d[k][0] - mean) <= 0.02 * mean, (d["era"], k, d[k][0], mean)
