@@ -266,11 +266,13 @@ int ahs_device_bytes(ahs_t *h, size_t *bytes);
 /* ---- batched ensembles ---------------------------------------------------
  * Many independent realisations (members) of possibly different sides N and
  * eras, sharing dx, dt, lambda0, e0, sigma and s, advanced together: every
- * leapfrog step is one persistent launch over the tiles of all members, and each
+ * leapfrog step is one persistent launch over the tiles of all members (a plain
+ * step: paired 64 x 8 tiles for members of even side, and a second launch on
+ * one-site tiles if some side is odd; a measuring step: one-site tiles), and each
  * measurement period (AHS_OPT_MEASURE_EVERY steps, 10 if measurements are off)
- * is replayed as one captured CUDA graph.  A member runs the same kernel and
- * coefficients as a single lattice, so its fields equal those of an ahs_t run of
- * the same seed and launch shape bit for bit.  All members start at n = 0; member
+ * is replayed as one captured CUDA graph.  A member runs the same kernels and
+ * coefficients as a single lattice, so its fields and records equal those of an
+ * ahs_t run of the same seed and launch shape bit for bit.  All members start at n = 0; member
  * m stops at its last step n_end[m] (default: half light-crossing, eta_end =
  * N dx / 2, Sec. 2) while the others continue.  Device memory: 80 bytes per site
  * of every member plus small tables; the batch owns a non-blocking stream. */
@@ -306,8 +308,9 @@ int ahs_batch_get_option(ahs_batch_t *b, int key, double *value);
 int ahs_batch_member_zchunk(ahs_batch_t *b, int m, int *dz);
 /* choose the tile height and each member size's z-chunk by timing the batched
  * plain step itself (CUDA events on the batch stream; the state is not changed):
- * per tile height, each size's z-chunk in turn with the others held fixed.
- * Needs an initialised batch. */
+ * per tile height, each size's z-chunk in turn with the others held fixed.  The
+ * tile height shapes the one-site tiles (members of odd side, measuring steps);
+ * when every side is even it stays 8.  Needs an initialised batch. */
 int ahs_batch_autotune(ahs_batch_t *b);
 /* with AHS_OPT_PROFILE: device time of ahs_batch_run calls (ms, CUDA events on the
  * batch stream) and the steps they advanced */

@@ -6,7 +6,11 @@
 // tile of ahs_step.cu) with the same FP64 per-step coefficients, so a member's
 // fields are bit-identical to a single-lattice run of the same seed and launch
 // shape.  Members stop at their own last step (half light-crossing, Sec. 2, by
-// default) while the others continue.
+// default) while the others continue.  Three work lists: the measuring steps of
+// all members on one-site 32 x by tiles (their partial rows are the rows of a
+// single lattice's measuring launch, so the records match too); the plain steps
+// of members of even side on paired 64 x 8 tiles (the single lattice's plain step
+// on even N); the plain steps of members of odd side on one-site tiles.
 #include "ahs_host.h"
 
 #include <algorithm>
@@ -57,10 +61,16 @@ struct ahs_batch {
 
     // device tables
     BatchMember *d_members = nullptr;
-    BatchTile *d_tiles = nullptr;
+    BatchTile *d_tiles = nullptr; // measuring steps: one-site tiles of every member
     int ntiles = 0;
     int *d_live = nullptr;        // live tiles per step
     int *d_tickets = nullptr;     // tile tickets per step
+    BatchTile *d_ptiles = nullptr;   // plain steps, even side: paired tiles
+    int nptiles = 0;
+    int *d_plive = nullptr, *d_ptickets = nullptr;
+    BatchTile *d_otiles = nullptr;   // plain steps, odd side: one-site tiles
+    int notiles = 0;
+    int *d_olive = nullptr, *d_otickets = nullptr;
     double *d_partials = nullptr;
     int rows_cap = 0;
     StepCoef *d_coef = nullptr;
@@ -75,7 +85,7 @@ struct ahs_batch {
     bool tables_dirty = true;
     bool tiles_dirty = true;
 
-    int grid_plain = 0, grid_meas = 0;
+    int grid_plain = 0, grid_meas = 0, grid_pair = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t gexec = nullptr;
@@ -111,12 +121,23 @@ namespace {
 
 int period(const ahs_batch_t *b) { return b->measure_every > 0 ? b->measure_every : 10; }
 
-void free_tables(ahs_batch_t *b)
+void free_lists(ahs_batch_t *b)
 {
     cudaFree(b->d_members); b->d_members = nullptr;
-    cudaFree(b->d_tiles); b->d_tiles = nullptr;
-    cudaFree(b->d_live); b->d_live = nullptr;
-    cudaFree(b->d_tickets); b->d_tickets = nullptr;
+    for (BatchTile **t : {&b->d_tiles, &b->d_ptiles, &b->d_otiles}) {
+        cudaFree(*t);
+        *t = nullptr;
+    }
+    for (int **a : {&b->d_live, &b->d_tickets, &b->d_plive, &b->d_ptickets, &b->d_olive, &b->d_otickets}) {
+        cudaFree(*a);
+        *a = nullptr;
+    }
+    b->ntiles = b->nptiles = b->notiles = 0;
+}
+
+void free_tables(ahs_batch_t *b)
+{
+    free_lists(b);
     cudaFree(b->d_partials); b->d_partials = nullptr;
     cudaFree(b->d_coef); b->d_coef = nullptr;
     cudaFree(b->d_obs); b->d_obs = nullptr;
@@ -147,12 +168,25 @@ StepPtrs member_ptrs(const ahs_batch_t *b, int m, int buf)
     return p;
 }
 
-// work list: members in decreasing order of their last step (ties: larger first),
+// work lists: members in decreasing order of their last step (ties: larger first),
 // each member's tiles in (z-chunk, y, x) order; live[n] counts the tiles of the
 // members with n < n_end, a prefix of the list
+int upload_list(ahs_batch_t *b, const std::vector<BatchTile> &tiles, const std::vector<int> &live, BatchTile **d_t,
+                int **d_live, int **d_tickets)
+{
+    const size_t steps = live.size();
+    if (tiles.empty()) return AHS_OK;
+    BCU(cudaMalloc(d_t, sizeof(BatchTile) * tiles.size()));
+    BCU(cudaMalloc(d_live, sizeof(int) * steps));
+    BCU(cudaMalloc(d_tickets, sizeof(int) * steps));
+    BCU(cudaMemcpy(*d_t, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice));
+    BCU(cudaMemcpy(*d_live, live.data(), sizeof(int) * steps, cudaMemcpyHostToDevice));
+    BCU(cudaMemset(*d_tickets, 0, sizeof(int) * steps));
+    return AHS_OK;
+}
+
 int build_tiles(ahs_batch_t *b)
 {
-    std::vector<BatchTile> tiles;
     b->members.assign(b->count, BatchMember{});
     std::vector<int> order(b->count);
     for (int m = 0; m < b->count; ++m) order[m] = m;
@@ -160,49 +194,59 @@ int build_tiles(ahs_batch_t *b)
         if (b->n_end[i] != b->n_end[j]) return b->n_end[i] > b->n_end[j];
         return b->prm[i].N > b->prm[j].N;
     });
-    for (int m : order) {
-        const int N = b->prm[m].N, dz = std::max(1, std::min(b->dz[m], N));
+    const int64_t steps = b->max_end() + 1;
+    // the tiles of the members `use` accepts, wx sites wide and by rows high
+    auto make = [&](auto use, int wx, int by, std::vector<BatchTile> &tiles, std::vector<int> &live, bool rows) {
+        live.assign((size_t)steps, 0);
+        for (int m : order) {
+            if (!use(m)) continue;
+            const int N = b->prm[m].N, dz = std::max(1, std::min(b->dz[m], N));
+            const int first = (int)tiles.size();
+            for (int z0 = 0; z0 < N; z0 += dz)
+                for (int y0 = 0; y0 < N; y0 += by)
+                    for (int x0 = 0; x0 < N; x0 += wx) tiles.push_back(BatchTile{m, x0, y0, z0, std::min(z0 + dz, N), 0});
+            const int cnt = (int)tiles.size() - first;
+            if (rows) {
+                b->members[m].row0 = first;
+                b->members[m].nrows = cnt;
+            }
+            for (int64_t n = 0; n < std::min<int64_t>(steps, b->n_end[m]); ++n) live[(size_t)n] += cnt;
+        }
+    };
+    for (int m = 0; m < b->count; ++m) {
         BatchMember &mb = b->members[m];
         mb.base = b->plane(m, 0, 0);
-        mb.N = N;
+        mb.N = b->prm[m].N;
         mb.n_end = b->n_end[m];
-        mb.row0 = (int)tiles.size();
-        for (int z0 = 0; z0 < N; z0 += dz)
-            for (int y0 = 0; y0 < N; y0 += b->by)
-                for (int x0 = 0; x0 < N; x0 += 32) tiles.push_back(BatchTile{m, x0, y0, z0, std::min(z0 + dz, N), 0});
-        mb.nrows = (int)tiles.size() - mb.row0;
     }
-    b->ntiles = (int)tiles.size();
-    const int64_t steps = b->max_end() + 1;
-    std::vector<int> live((size_t)steps, 0);
-    for (int64_t n = 0; n < steps; ++n)
-        for (int m = 0; m < b->count; ++m)
-            if (n < b->n_end[m]) live[(size_t)n] += b->members[m].nrows;
-    cudaFree(b->d_members);
-    cudaFree(b->d_tiles);
-    cudaFree(b->d_live);
-    cudaFree(b->d_tickets);
-    b->d_members = nullptr;
-    b->d_tiles = nullptr;
-    b->d_live = nullptr;
-    b->d_tickets = nullptr;
-    BCU(cudaMalloc(&b->d_members, sizeof(BatchMember) * b->count));
-    BCU(cudaMalloc(&b->d_tiles, sizeof(BatchTile) * tiles.size()));
-    BCU(cudaMalloc(&b->d_live, sizeof(int) * (size_t)steps));
-    BCU(cudaMalloc(&b->d_tickets, sizeof(int) * (size_t)steps));
-    BCU(cudaMemcpy(b->d_live, live.data(), sizeof(int) * (size_t)steps, cudaMemcpyHostToDevice));
-    BCU(cudaMemset(b->d_tickets, 0, sizeof(int) * (size_t)steps));
+    std::vector<BatchTile> tm, tp, to;
+    std::vector<int> lm, lp, lo;
+    make([](int) { return true; }, 32, b->by, tm, lm, true);
+    make([&](int m) { return b->prm[m].N % 2 == 0; }, 64, 8, tp, lp, false);
+    make([&](int m) { return b->prm[m].N % 2 != 0; }, 32, b->by, to, lo, false);
+    BatchMember *keep_members = nullptr;
+    std::swap(keep_members, b->d_members);
+    free_lists(b);
+    b->d_members = keep_members;
+    if (!b->d_members) BCU(cudaMalloc(&b->d_members, sizeof(BatchMember) * b->count));
     BCU(cudaMemcpy(b->d_members, b->members.data(), sizeof(BatchMember) * b->count, cudaMemcpyHostToDevice));
-    BCU(cudaMemcpy(b->d_tiles, tiles.data(), sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice));
+    if (int r = upload_list(b, tm, lm, &b->d_tiles, &b->d_live, &b->d_tickets)) return r;
+    if (int r = upload_list(b, tp, lp, &b->d_ptiles, &b->d_plive, &b->d_ptickets)) return r;
+    if (int r = upload_list(b, to, lo, &b->d_otiles, &b->d_olive, &b->d_otickets)) return r;
+    b->ntiles = (int)tm.size();
+    b->nptiles = (int)tp.size();
+    b->notiles = (int)to.size();
     if (b->ntiles > b->rows_cap) {
         cudaFree(b->d_partials);
         b->d_partials = nullptr;
         BCU(cudaMalloc(&b->d_partials, sizeof(double) * NQ * (size_t)b->ntiles));
         b->rows_cap = b->ntiles;
     }
-    b->grid_plain = std::min(batch_grid(b->by, false), b->ntiles);
     b->grid_meas = std::min(batch_grid(b->by, true), b->ntiles);
-    if (b->grid_plain < 1 || b->grid_meas < 1) return bfail(AHS_ECUDA, "cannot size the persistent batch launch");
+    b->grid_plain = b->notiles ? std::min(batch_grid(b->by, false), b->notiles) : 0;
+    b->grid_pair = b->nptiles ? std::min(batch_pair_grid(), b->nptiles) : 0;
+    if (b->grid_meas < 1 || (b->notiles && b->grid_plain < 1) || (b->nptiles && b->grid_pair < 1))
+        return bfail(AHS_ECUDA, "cannot size the persistent batch launch");
     b->tiles_dirty = false;
     drop_graph(b);
     return AHS_OK;
@@ -239,13 +283,15 @@ int build_tables(ahs_batch_t *b)
     return AHS_OK;
 }
 
-BatchLaunch launch_args(const ahs_batch_t *b)
+// the launch arguments of one work list: measuring (0), plain paired (1), plain
+// one-site of odd sides (2)
+BatchLaunch launch_args(const ahs_batch_t *b, int list = 0)
 {
     BatchLaunch L;
-    L.tiles = b->d_tiles;
-    L.ntiles = b->ntiles;
-    L.live = b->d_live;
-    L.tickets = b->d_tickets;
+    L.tiles = list == 1 ? b->d_ptiles : list == 2 ? b->d_otiles : b->d_tiles;
+    L.ntiles = list == 1 ? b->nptiles : list == 2 ? b->notiles : b->ntiles;
+    L.live = list == 1 ? b->d_plive : list == 2 ? b->d_olive : b->d_live;
+    L.tickets = list == 1 ? b->d_ptickets : list == 2 ? b->d_otickets : b->d_tickets;
     L.members = b->d_members;
     L.nmembers = b->count;
     L.coef = b->d_coef;
@@ -255,6 +301,16 @@ BatchLaunch launch_args(const ahs_batch_t *b)
     return L;
 }
 
+// one plain step of every member: the paired launch (even sides) and the one-site
+// launch (odd sides), each only if it has tiles
+cudaError_t enqueue_plain(const ahs_batch_t *b, int d, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    if (b->nptiles) e = launch_batch_pair_step(launch_args(b, 1), d, b->grid_pair, st);
+    if (e == cudaSuccess && b->notiles) e = launch_batch_step(launch_args(b, 2), b->by, d, false, b->grid_plain, st);
+    return e;
+}
+
 // enqueue steps n .. n+len-1 (the first measures when it is a measurement step)
 cudaError_t enqueue_steps(ahs_batch_t *b, int64_t n0, int len, cudaStream_t st)
 {
@@ -262,7 +318,7 @@ cudaError_t enqueue_steps(ahs_batch_t *b, int64_t n0, int len, cudaStream_t st)
     const int G = b->measure_every;
     for (int d = 0; d < len; ++d) {
         const bool meas = G > 0 && ((n0 + d) % G == 0);
-        cudaError_t e = launch_batch_step(L, b->by, d, meas, meas ? b->grid_meas : b->grid_plain, st);
+        cudaError_t e = meas ? launch_batch_step(L, b->by, d, true, b->grid_meas, st) : enqueue_plain(b, d, st);
         if (e != cudaSuccess) return e;
         if (meas) {
             e = launch_batch_reduce(b->d_partials, b->d_members, b->count, b->d_obs, b->obs_stride, b->d_counter, d, G,
@@ -415,7 +471,8 @@ int ahs_batch_init(ahs_batch_t *b)
     }
     b->n = 0;
     BCU(cudaMemsetAsync(b->d_counter, 0, sizeof(int64_t), b->stream));
-    if (b->d_tickets) BCU(cudaMemsetAsync(b->d_tickets, 0, sizeof(int) * (size_t)(b->max_end() + 1), b->stream));
+    for (int *t : {b->d_tickets, b->d_ptickets, b->d_otickets})
+        if (t) BCU(cudaMemsetAsync(t, 0, sizeof(int) * (size_t)(b->max_end() + 1), b->stream));
     BCU(cudaStreamSynchronize(b->stream));
     for (auto &l : b->log) l.clear();
     b->ready = true;
@@ -666,10 +723,11 @@ int ahs_batch_member_zchunk(ahs_batch_t *b, int m, int *dz)
     return report_ok();
 }
 
-// Time one plain batched step (the persistent launch over all members, CUDA
+// Time one plain batched step (the persistent launches over all members, CUDA
 // events, state unchanged: the step reads one buffer and writes the other and the
-// step counter is not advanced) for each tile height, and then per member size
-// for each z-chunk with the other sizes held fixed; keep the fastest.
+// step counter is not advanced) for each tile height (8 only when every side is
+// even), and then per member size for each z-chunk with the other sizes held
+// fixed; keep the fastest.
 int ahs_batch_autotune(ahs_batch_t *b)
 {
     if (!b) return bfail(AHS_EINVAL, "null batch");
@@ -680,15 +738,19 @@ int ahs_batch_autotune(ahs_batch_t *b)
     auto time_step = [&](float *out) -> int {
         if (b->tiles_dirty)
             if (int r = build_tiles(b)) return r;
-        const BatchLaunch L = launch_args(b);
-        int *ticket = b->d_tickets + std::min<int64_t>(b->n, b->max_end());   // the step's tile counter
-        BCU(cudaMemsetAsync(ticket, 0, sizeof(int), b->stream));
-        BCU(launch_batch_step(L, b->by, 0, false, b->grid_plain, b->stream));   // warm-up
+        const int64_t n = std::min<int64_t>(b->n, b->max_end());   // the step's tile counters
+        auto reset = [&]() -> int {
+            for (int *t : {b->d_ptickets, b->d_otickets})
+                if (t) BCU(cudaMemsetAsync(t + n, 0, sizeof(int), b->stream));
+            return AHS_OK;
+        };
+        if (int r = reset()) return r;
+        BCU(enqueue_plain(b, 0, b->stream));   // warm-up
         float best = 1e30f, ms = 0.f;
         for (int rep = 0; rep < 3; ++rep) {
-            BCU(cudaMemsetAsync(ticket, 0, sizeof(int), b->stream));
+            if (int r = reset()) return r;
             BCU(cudaEventRecord(b->ev0, b->stream));
-            BCU(launch_batch_step(L, b->by, 0, false, b->grid_plain, b->stream));
+            BCU(enqueue_plain(b, 0, b->stream));
             BCU(cudaEventRecord(b->ev1, b->stream));
             BCU(cudaEventSynchronize(b->ev1));
             BCU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
@@ -704,7 +766,12 @@ int ahs_batch_autotune(ahs_batch_t *b)
     float best_total = 1e30f;
     int best_by = b->by;
     std::vector<int> best_dz = b->dz;
+    // the tile height shapes only the one-site plain tiles (members of odd side) of
+    // a plain step; without those the measuring steps keep 8-row tiles
+    bool any_odd = false;
+    for (auto &p : b->prm) any_odd = any_odd || p.N % 2 != 0;
     for (int by : {8, 16}) {
+        if (by == 16 && !any_odd) break;
         b->by = by;
         for (int m = 0; m < b->count; ++m) b->dz[m] = std::min(32, b->prm[m].N);
         b->tiles_dirty = true;

@@ -143,6 +143,10 @@ struct BatchLaunch {
 };
 cudaError_t launch_batch_step(const BatchLaunch &L, int by, int dn, bool measure, int grid, cudaStream_t st);
 int batch_grid(int by, bool measure);   // resident CTAs of the persistent launch
+// the plain step of members of even side on paired 64 x 8 tiles (tiles of the list
+// start at x0 multiples of 64), and its resident CTAs
+cudaError_t launch_batch_pair_step(const BatchLaunch &L, int dn, int grid, cudaStream_t st);
+int batch_pair_grid();
 // per-member measurement record of step *counter + dn when that step is a
 // measurement step of the member: records[m * rcap + n / every]
 cudaError_t launch_batch_reduce(const double *partials, const BatchMember *members, int nmembers,

@@ -61,20 +61,28 @@ struct ParamFields {
     using real = float;
     const StepPtrs &P;
     uint32_t V;   // sites per plane (N^3): the extent of the bounds-check build's offset checks
-    __device__ __forceinline__ float in(int f, uint32_t o) const
+    __device__ __forceinline__ const float *src(int f) const
     {
-        o = AHS_INDEX(o, V);
-        const float *p = f == FPR ? P.pr : f == FPI ? P.pim : f == FQR ? P.qr : f == FQI ? P.qi : f == FTX ? P.tx
-                       : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : f == FEZ ? P.ez
-                       : f == FQRL ? P.qrl : f == FQIL ? P.qil : f == FEXL ? P.exl : f == FEYL ? P.eyl : P.ezl;
-        return __ldg(p + o);
+        return f == FPR ? P.pr : f == FPI ? P.pim : f == FQR ? P.qr : f == FQI ? P.qi : f == FTX ? P.tx
+             : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : f == FEZ ? P.ez
+             : f == FQRL ? P.qrl : f == FQIL ? P.qil : f == FEXL ? P.exl : f == FEYL ? P.eyl : P.ezl;
     }
-    __device__ __forceinline__ void out(int f, uint32_t o, float v) const
+    __device__ __forceinline__ float *dst(int f) const
     {
-        float *p = f == FPR ? P.pr1 : f == FPI ? P.pim1 : f == FQR ? P.qr1 : f == FQI ? P.qi1 : f == FTX ? P.tx1
-                 : f == FTY ? P.ty1 : f == FTZ ? P.tz1 : f == FEX ? P.ex1 : f == FEY ? P.ey1 : f == FEZ ? P.ez1
-                 : f == FQRL ? P.qrl1 : f == FQIL ? P.qil1 : f == FEXL ? P.exl1 : f == FEYL ? P.eyl1 : P.ezl1;
-        p[AHS_INDEX(o, V)] = v;
+        return f == FPR ? P.pr1 : f == FPI ? P.pim1 : f == FQR ? P.qr1 : f == FQI ? P.qi1 : f == FTX ? P.tx1
+             : f == FTY ? P.ty1 : f == FTZ ? P.tz1 : f == FEX ? P.ex1 : f == FEY ? P.ey1 : f == FEZ ? P.ez1
+             : f == FQRL ? P.qrl1 : f == FQIL ? P.qil1 : f == FEXL ? P.exl1 : f == FEYL ? P.eyl1 : P.ezl1;
+    }
+    __device__ __forceinline__ float in(int f, uint32_t o) const { return __ldg(src(f) + AHS_INDEX(o, V)); }
+    __device__ __forceinline__ void out(int f, uint32_t o, float v) const { dst(f)[AHS_INDEX(o, V)] = v; }
+    // sites o and o+1 as one 8-byte access (o even, planes 8-byte aligned)
+    __device__ __forceinline__ float2 in2(int f, uint32_t o) const
+    {
+        return __ldg(reinterpret_cast<const float2 *>(src(f) + AHS_INDEX(o, V - 1)));
+    }
+    __device__ __forceinline__ void out2(int f, uint32_t o, float a, float b) const
+    {
+        *reinterpret_cast<float2 *>(dst(f) + AHS_INDEX(o, V - 1)) = make_float2(a, b);
     }
 };
 
@@ -89,6 +97,17 @@ struct ArenaFields {
     __device__ __forceinline__ void out(int f, uint32_t o, float v) const
     {
         const_cast<float *>(base)[out0 + (uint32_t)f * V + AHS_INDEX(o, V)] = v;
+    }
+    // sites o and o+1 as one 8-byte access (o even; every member's planes start on
+    // an 8-byte boundary when its N is even)
+    __device__ __forceinline__ float2 in2(int f, uint32_t o) const
+    {
+        return __ldg(reinterpret_cast<const float2 *>(base + (in0 + (uint32_t)f * V + AHS_INDEX(o, V - 1))));
+    }
+    __device__ __forceinline__ void out2(int f, uint32_t o, float a, float b) const
+    {
+        *reinterpret_cast<float2 *>(const_cast<float *>(base) + (out0 + (uint32_t)f * V + AHS_INDEX(o, V - 1))) =
+            make_float2(a, b);
     }
 };
 

@@ -583,18 +583,16 @@ struct Tile2 {
     static __device__ __forceinline__ int q(int ex, int ey) { return AHS_INDEX((ey + 1) * SXP + (ex + 2), NS); }
 };
 
-template <int BY>
-__global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCoef k, int N, int Dz)
+// One paired tile: the 64 x BY column at (x0, y0), planes [z0, zend), plain step.
+// All threads of the CTA call it together (it contains CTA barriers).
+template <int BY, class FA>
+__device__ __forceinline__ void pair_tile(typename Tile2<BY>::Smem &S, const FA &F, const StepCoef &k, int N, int x0,
+                                          int y0, int z0, int zend)
 {
     using T = Tile2<BY>;
     using V2 = float2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
     const int tx = threadIdx.x, ty = threadIdx.y, t = tx + 32 * ty;
-    const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
-    const int zend = min(z0 + Dz, N);
     const uint32_t NN = (uint32_t)N * (uint32_t)N;
-    const ParamFields F{P, NN * (uint32_t)N};
 
     // core pair: sites ex and ex+1 of row ty
     const int ex = 2 * tx;
@@ -617,13 +615,6 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
     const bool hasB = ringRow || (t >= 2 * T::RX && t < 2 * T::RX + BY);
     const int hbx = ringRow ? t - 1 : -1, hby = ringRow ? -1 : t - 2 * T::RX;
 
-    // a pair is two floats: o + 1 must lie in the plane as well
-    auto ld2 = [&](const float *p, uint32_t o) {
-        return __ldg(reinterpret_cast<const float2 *>(p + AHS_INDEX(o, F.V - 1)));
-    };
-    auto st2 = [&](float *p, uint32_t o, float a, float b) {
-        *reinterpret_cast<float2 *>(p + AHS_INDEX(o, F.V - 1)) = make_float2(a, b);
-    };
     struct Raw2 {
         float2 tx, ty, tz, pr, pi;   // .x site ex, .y site ex+1
     };
@@ -632,14 +623,14 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
     };
     auto load_raw2 = [&](uint32_t o) {
         Raw2 a;
-        a.tx = ld2(P.tx, o); a.ty = ld2(P.ty, o); a.tz = ld2(P.tz, o);
-        a.pr = ld2(P.pr, o); a.pi = ld2(P.pim, o);
+        a.tx = F.in2(FTX, o); a.ty = F.in2(FTY, o); a.tz = F.in2(FTZ, o);
+        a.pr = F.in2(FPR, o); a.pi = F.in2(FPI, o);
         return a;
     };
     auto load_pe2 = [&](uint32_t o) {
         PE2 a;
-        a.qr = ld2(P.qr, o); a.qi = ld2(P.qi, o);
-        a.ex = ld2(P.ex, o); a.ey = ld2(P.ey, o); a.ez = ld2(P.ez, o);
+        a.qr = F.in2(FQR, o); a.qi = F.in2(FQI, o);
+        a.ex = F.in2(FEX, o); a.ey = F.in2(FEY, o); a.ez = F.in2(FEZ, o);
         return a;
     };
     auto phaseA2 = [&](const Raw2 &a, typename T::Plane &pl) {
@@ -770,13 +761,13 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
                 vz0s[j] = vz0;
             }
             const uint32_t o = oc + coff;
-            st2(P.qr1, o, qn[0][0], qn[1][0]);
-            st2(P.qi1, o, qn[0][1], qn[1][1]);
-            st2(P.ex1, o, en[0][0], en[1][0]);
-            st2(P.ey1, o, en[0][1], en[1][1]);
-            st2(P.ez1, o, en[0][2], en[1][2]);
-            st2(P.pr1, o, p0s[0].x + k.dphi * qn[0][0], p0s[1].x + k.dphi * qn[1][0]);
-            st2(P.pim1, o, p0s[0].y + k.dphi * qn[0][1], p0s[1].y + k.dphi * qn[1][1]);
+            F.out2(FQR, o, qn[0][0], qn[1][0]);
+            F.out2(FQI, o, qn[0][1], qn[1][1]);
+            F.out2(FEX, o, en[0][0], en[1][0]);
+            F.out2(FEY, o, en[0][1], en[1][1]);
+            F.out2(FEZ, o, en[0][2], en[1][2]);
+            F.out2(FPR, o, p0s[0].x + k.dphi * qn[0][0], p0s[1].x + k.dphi * qn[1][0]);
+            F.out2(FPI, o, p0s[0].y + k.dphi * qn[0][1], p0s[1].y + k.dphi * qn[1][1]);
             float t1[2][3];
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -789,9 +780,9 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
                     t1[j][2] += kTwoPiF * floorf((kPiF - t1[j][2]) * kInvTwoPiF);
                 }
             }
-            st2(P.tx1, o, t1[0][0], t1[1][0]);
-            st2(P.ty1, o, t1[0][1], t1[1][1]);
-            st2(P.tz1, o, t1[0][2], t1[1][2]);
+            F.out2(FTX, o, t1[0][0], t1[1][0]);
+            F.out2(FTY, o, t1[0][1], t1[1][1]);
+            F.out2(FTZ, o, t1[0][2], t1[1][2]);
         } else {
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -811,6 +802,62 @@ __global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCo
         zc = z1; z1 = z2; z2 = next_plane(z2, N);
         b = bn;
     }
+}
+
+template <int BY>
+__global__ void __launch_bounds__(32 * BY, 16 / BY) step_pair(StepPtrs P, StepCoef k, int N, int Dz)
+{
+    using T = Tile2<BY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
+    const int x0 = blockIdx.x * T::BX, y0 = blockIdx.y * BY, z0 = blockIdx.z * Dz;
+    pair_tile<BY>(S, ParamFields{P, (uint32_t)N * (uint32_t)N * (uint32_t)N}, k, N, x0, y0, z0, min(z0 + Dz, N));
+}
+
+// Persistent batched plain step on paired tiles (members of even side): the
+// ticketed loop of batch_step over a list of 64 x BY tiles.
+template <int BY>
+__global__ void __launch_bounds__(32 * BY, 16 / BY) batch_pair_step(BatchLaunch L, int dn)
+{
+    using T = Tile2<BY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename T::Smem &S = *reinterpret_cast<typename T::Smem *>(smem_raw);
+    __shared__ StepCoef sk;
+    __shared__ int s_w;
+    const int64_t n = *L.counter + dn;
+    const int par = (int)(n & 1);
+    const int live = L.live[n];
+    const int t = threadIdx.x + 32 * threadIdx.y;
+    for (;;) {
+        __syncthreads();   // everyone is done with s_w, sk and the shared planes of the previous tile
+        if (t == 0) s_w = atomicAdd(L.tickets + n, 1);
+        __syncthreads();
+        const int w = s_w;
+        if (w >= live) break;
+        const BatchTile tl = L.tiles[w];
+        const BatchMember &m = L.members[tl.member];
+        if (t < (int)(sizeof(StepCoef) / sizeof(float)))
+            reinterpret_cast<float *>(&sk)[t] = reinterpret_cast<const float *>(L.coef + (size_t)tl.member * L.coef_stride + n)[t];
+        const uint32_t V = (uint32_t)m.N * (uint32_t)m.N * (uint32_t)m.N;
+        const ArenaFields fa{m.base, par ? 10u * V : 0u, par ? 0u : 10u * V, V};
+        __syncthreads();
+        pair_tile<BY>(S, fa, sk, m.N, tl.x0, tl.y0, tl.z0, tl.zend);
+    }
+}
+
+int batch_pair_occupancy()
+{
+    using T = Tile2<8>;
+    const size_t bytes = sizeof(typename T::Smem);
+    if (cudaFuncSetAttribute(batch_pair_step<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return 0;
+    int per_sm = 0, dev = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_pair_step<8>, 256, bytes) != cudaSuccess)
+        return 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return per_sm * sms;
 }
 
 template <int BY>
@@ -906,6 +953,17 @@ int batch_grid(int by, bool measure)
 {
     if (by == 16) return measure ? batch_occupancy<16, true>() : batch_occupancy<16, false>();
     return measure ? batch_occupancy<8, true>() : batch_occupancy<8, false>();
+}
+
+int batch_pair_grid() { return batch_pair_occupancy(); }
+
+cudaError_t launch_batch_pair_step(const BatchLaunch &L, int dn, int grid, cudaStream_t st)
+{
+    // the dynamic shared-memory limit was raised by batch_pair_grid() when the
+    // launch was sized, before any launch or graph capture
+    if (grid < 1) return cudaErrorInvalidConfiguration;
+    batch_pair_step<8><<<grid, dim3(32, 8), sizeof(typename Tile2<8>::Smem), st>>>(L, dn);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_step(const BatchLaunch &L, int by, int dn, bool measure, int grid, cudaStream_t st)

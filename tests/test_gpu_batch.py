@@ -12,6 +12,8 @@ PARAMS = dict(dx=0.5, dt=0.1, lambda0=2.0, e0=1.0, sigma=1.0)
 MEMBERS = [  # (N, era, seed, n_end)
     (16, 1, 11, 25), (24, 2, 12, 17), (20, 0, 13, 30), (36, 1, 14, 22), (8, 2, 15, 9),
 ]
+# odd and even sides: a plain step runs the paired launch and the one-site launch
+MIXED = [(15, 1, 21, 19), (16, 2, 22, 23), (21, 0, 23, 12), (66, 1, 24, 16), (5, 2, 25, 21), (33, 1, 26, 14)]
 
 
 @pytest.fixture(scope="module")
@@ -34,16 +36,16 @@ def make_batch(pkg, members=MEMBERS, measure_every=5):
     return pkg.Batch(N, era, seed, list(end), measure_every=measure_every, **PARAMS)
 
 
-@pytest.mark.parametrize("graph", [1, 0])
-def test_batch_equals_single_runs(pkg, graph):
+@pytest.mark.parametrize("graph,members", [(1, MEMBERS), (0, MEMBERS), (1, MIXED), (0, MIXED)])
+def test_batch_equals_single_runs(pkg, graph, members):
     from paper_2005_14454_gb300._abi import AHS_OPT_GRAPH
-    with make_batch(pkg) as b:
+    with make_batch(pkg, members=members) as b:
         b.set_option(AHS_OPT_GRAPH, graph)
         b.init()
         done = b.run()
-        assert done == max(m[3] for m in MEMBERS)
+        assert done == max(m[3] for m in members)
         assert b.run() == 0
-        for i, (N, era, seed, end) in enumerate(MEMBERS):
+        for i, (N, era, seed, end) in enumerate(members):
             n, n_end = b.step_info(i)
             assert n == n_end == end
             F, rec = single(pkg, N, era, seed, end)
@@ -81,18 +83,22 @@ def test_batch_member_matches_oracle(pkg, orc):
             assert max(se.values()) < 5e-6, se
 
 
-def test_batch_autotune_keeps_results(pkg):
-    from paper_2005_14454_gb300._abi import AHS_OPT_TILE_Y, ahs_batch_member_zchunk
-    with make_batch(pkg) as a, make_batch(pkg) as b:
+@pytest.mark.parametrize("members", [MEMBERS, MIXED])
+def test_batch_autotune_keeps_results(pkg, members):
+    from paper_2005_14454_gb300._abi import AHS_OPT_TILE_Y, ahs_batch_get_option, ahs_batch_member_zchunk
+    with make_batch(pkg, members=members) as a, make_batch(pkg, members=members) as b:
         a.init()
         b.init()
         b.autotune()
-        assert b.b and int(__import__("paper_2005_14454_gb300")._abi.ahs_batch_get_option(b.b, AHS_OPT_TILE_Y)) in (8, 16)
-        assert all(ahs_batch_member_zchunk(b.b, i) >= 1 for i in range(len(MEMBERS)))
+        by = int(ahs_batch_get_option(b.b, AHS_OPT_TILE_Y))
+        # the tile height only shapes the one-site plain tiles of odd sides
+        assert by in ((8, 16) if any(m[0] % 2 for m in members) else (8,))
+        assert all(ahs_batch_member_zchunk(b.b, i) >= 1 for i in range(len(members)))
         a.run()
         b.run()
-        for i in range(len(MEMBERS)):
+        for i in range(len(members)):
             assert np.array_equal(a.state(i), b.state(i))
+            assert a.records(i)[-1]["n_wind"] == b.records(i)[-1]["n_wind"]
 
 
 def test_batch_set_fields_and_nonfinite(pkg):
