@@ -16,6 +16,63 @@ constexpr double kPiD = 3.141592653589793238;
 // is recomputed in FP64 with the operations in the order of the definition.
 constexpr float kTie = 1e-4f;
 
+// ---------------------------------------------------------------- index checks
+// The bounds-check build of the library (-DAHS_BOUNDS_CHECK, _ahs_check.so) checks
+// every global offset of the step kernels' tile loaders, rings and stores and every
+// shared-memory index of their tiles against the extent it addresses.  An index
+// outside it is counted in g_bounds_errors (one counter per translation unit, read
+// by ahs_bounds_check) and replaced by 0, so the access stays in range: nothing
+// traps, and nothing is read or written outside its array.  The production build
+// compiles the checks away.
+#ifdef AHS_BOUNDS_CHECK
+static __device__ unsigned long long g_bounds_errors;
+static __device__ __forceinline__ uint32_t checked_index(uint32_t i, uint32_t n)
+{
+    if (i >= n) {
+        atomicAdd(&g_bounds_errors, 1ull);
+        return 0u;
+    }
+    return i;
+}
+static __device__ __forceinline__ int checked_index(int i, int n)
+{
+    if (i < 0 || i >= n) {
+        atomicAdd(&g_bounds_errors, 1ull);
+        return 0;
+    }
+    return i;
+}
+#define AHS_INDEX(i, n) ::eng::checked_index((i), (n))
+// host side: this translation unit's counter on the current device (read, then
+// zeroed if reset), and a self-test launch that passes one index outside its extent
+// through the check (touching no memory)
+static __global__ void bounds_selftest_kernel()
+{
+    (void)checked_index(7, 3);
+}
+#define AHS_BOUNDS_COUNTER(name)                                                                     \
+    cudaError_t name(unsigned long long *count, int op)                                            \
+    {                                                                                              \
+        if (op == 2) {                                                                             \
+            bounds_selftest_kernel<<<1, 1>>>();                                                    \
+            cudaError_t e = cudaDeviceSynchronize();                                               \
+            if (e != cudaSuccess) return e;                                                        \
+        }                                                                                          \
+        cudaError_t e = cudaMemcpyFromSymbol(count, g_bounds_errors, sizeof(*count));              \
+        if (e != cudaSuccess || op == 0) return e;                                                 \
+        const unsigned long long zero = 0;                                                         \
+        return cudaMemcpyToSymbol(g_bounds_errors, &zero, sizeof(zero));                           \
+    }
+#else
+#define AHS_INDEX(i, n) (i)
+#define AHS_BOUNDS_COUNTER(name)                                                                     \
+    cudaError_t name(unsigned long long *count, int)                                               \
+    {                                                                                              \
+        *count = 0;                                                                                \
+        return cudaErrorNotSupported;                                                              \
+    }
+#endif
+
 // ---------------------------------------------------------------- link phases
 // (cos th, sin th) of a link angle (Eq. 13) without the library sincosf: th is
 // reduced to r = th - k pi, |r| <= pi/2, k = rint(th / pi), with pi split into two
@@ -181,6 +238,96 @@ static __device__ __forceinline__ int winding(int o1, int o2, int o3, int o4, in
     return (2 * t + 9) >> 4;
 }
 
+// ---------------------------------------------------------------- flagged codes
+// The fused measurement keeps each angle as a flagged code: bits 0-2 its octant + 4
+// (0..7, from the float value), bit 3 set when the value is too close to the branch
+// cut for that octant to be trusted (near_cut).  A plaquette whose five codes carry
+// no flag has the winding winding_codes gives; a site any of whose phases is flagged
+// (a few in 10^4 sites) recomputes the flagged ones in FP64 (site_windings_flagged).
+// Both give the winding of the definition: the octants of the exact angles agree with
+// these to within one octant, which the pi/5 margin of winding() absorbs, and at the
+// cut FP64 decides.
+template <class R>
+static __device__ __forceinline__ int flagged_octant(R zr, R zi)
+{
+    return (octant(zr, zi) + 4) | (near_cut(zr, zi) ? 8 : 0);
+}
+
+// Y_i(x) as a flagged code from V_i = (cos theta_i, sin theta_i): arg of conj(p) U_i q
+template <class R>
+static __device__ __forceinline__ int link_code(R pr, R pi, R qr, R qi, R vc, R vs)
+{
+    const R hr = vc * qr + vs * qi;   // U_i q with U_i = vc - i vs
+    const R hi = vc * qi - vs * qr;
+    const R zr = pr * hr + pi * hi;   // conj(p) U_i q
+    const R zi = pr * hi - pi * hr;
+    return flagged_octant(zr, zi);
+}
+
+// winding() of five flagged codes (flags ignored: the caller checks them); the
+// offsets of 4 cancel in c1 + c2 - c3 - c4 and one is left from ca
+static __device__ __forceinline__ int winding_codes(int c1, int c2, int c3, int c4, int ca)
+{
+    const int t = (c1 & 7) + (c2 & 7) - (c3 & 7) - (c4 & 7) + (ca & 7) - 4;
+    return (2 * t + 9) >> 4;
+}
+
+// Octant code of an FP64 complex number with the signs taken as atan2 takes them
+// (a signed zero decides the side of the branch cut: arg(-1 + 0i) = pi, arg(-1 - 0i)
+// = -pi), so no arctangent is needed.
+static __device__ __forceinline__ int octant_signed(double zr, double zi)
+{
+    const bool steep = fabs(zi) > fabs(zr), ny = signbit(zi), nx = signbit(zr);
+    if (!ny) return !nx ? (steep ? 1 : 0) : (steep ? 2 : 3);
+    return !nx ? (steep ? -2 : -1) : (steep ? -3 : -4);
+}
+
+// The windings W_xy, W_xz, W_yz of the plaquettes with lower corner x from the flagged
+// codes of their phases, each flagged phase recomputed in FP64 from the fields (planes
+// pr, pi, tx, ty, tz of N^3 = V sites, read at the offsets o0 .. o6 of x, x+x, x+y,
+// x+z, x+x+y, x+x+z, x+y+z): a link phase from the FP64 polynomial link phase of its
+// angle and the FP64 product conj(p) U q, a plaquette angle by wrap_plaq_fp64 of its
+// four link angles.  codes holds twelve 4-bit codes (code k in bits 4k..4k+3) in the
+// order Y_x, Y_y, Y_z at x; Y_y at x+x; Y_x at x+y; Y_z at x+x; Y_z at x+y; Y_x at
+// x+z; Y_y at x+z; alpha_xy, alpha_xz, alpha_yz.  The rare path of the fused
+// measurement: plain pointers and values only, so that the caller keeps its field
+// access in registers.
+template <class In>
+static __device__ __noinline__ int3 site_windings_flagged(const In *pr, const In *pim, const In *tx, const In *ty,
+                                                          const In *tz, uint32_t V, uint32_t o0, uint32_t o1,
+                                                          uint32_t o2, uint32_t o3, uint32_t o4, uint32_t o5,
+                                                          uint32_t o6, unsigned long long codes)
+{
+    const uint32_t o[7] = {AHS_INDEX(o0, V), AHS_INDEX(o1, V), AHS_INDEX(o2, V), AHS_INDEX(o3, V),
+                           AHS_INDEX(o4, V), AHS_INDEX(o5, V), AHS_INDEX(o6, V)};
+    const In *th[3] = {tx, ty, tz};
+    auto code = [&](int k) { return (int)((codes >> (4 * k)) & 15u); };
+    auto Y = [&](int k, int a, int b, int f) {   // Y_f at site a, towards site b = a + f
+        const int c = code(k);
+        if (!(c & 8)) return (c & 7) - 4;
+        double sn, cs;
+        link_sincos((double)th[f][o[a]], sn, cs);
+        const double p0 = pr[o[a]], p1 = pim[o[a]], q0 = pr[o[b]], q1 = pim[o[b]];
+        const double hr = __dadd_rn(__dmul_rn(cs, q0), __dmul_rn(sn, q1));   // U q, U = cos - i sin
+        const double hi = __dsub_rn(__dmul_rn(cs, q1), __dmul_rn(sn, q0));
+        const double zr = __dadd_rn(__dmul_rn(p0, hr), __dmul_rn(p1, hi));   // conj(p) U q
+        const double zi = __dsub_rn(__dmul_rn(p0, hi), __dmul_rn(p1, hr));
+        return octant_signed(zr, zi);
+    };
+    auto A = [&](int k, int i, int j) {   // [alpha_ij]_pi at x: links i, j at x, x+i, x+j
+        const int c = code(k);
+        if (!(c & 8)) return (c & 7) - 4;
+        const int oi = i == 0 ? 1 : 2, oj = j == 1 ? 2 : 3;   // x+i, x+j
+        return octant(wrap_plaq_fp64(th[i][o[0]], th[j][o[oi]], th[i][o[oj]], th[j][o[0]]));
+    };
+    const int yx = Y(0, 0, 1, 0), yy = Y(1, 0, 2, 1), yz = Y(2, 0, 3, 2);
+    int3 w;
+    w.x = winding(yx, Y(3, 1, 4, 1), Y(4, 2, 4, 0), yy, A(9, 0, 1));
+    w.y = winding(yx, Y(5, 1, 5, 2), Y(7, 3, 5, 0), yz, A(10, 0, 2));
+    w.z = winding(yy, Y(6, 2, 6, 2), Y(8, 3, 6, 1), yz, A(11, 1, 2));
+    return w;
+}
+
 // SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): one step from state v.
 static __device__ __forceinline__ uint64_t splitmix64_device(uint64_t v)
 {
@@ -194,63 +341,6 @@ static __device__ __forceinline__ size_t sidx(int x, int y, int z, int N)
 {
     return (size_t)x + (size_t)N * ((size_t)y + (size_t)N * (size_t)z);
 }
-
-// ---------------------------------------------------------------- index checks
-// The bounds-check build of the library (-DAHS_BOUNDS_CHECK, _ahs_check.so) checks
-// every global offset of the step kernels' tile loaders, rings and stores and every
-// shared-memory index of their tiles against the extent it addresses.  An index
-// outside it is counted in g_bounds_errors (one counter per translation unit, read
-// by ahs_bounds_check) and replaced by 0, so the access stays in range: nothing
-// traps, and nothing is read or written outside its array.  The production build
-// compiles the checks away.
-#ifdef AHS_BOUNDS_CHECK
-static __device__ unsigned long long g_bounds_errors;
-static __device__ __forceinline__ uint32_t checked_index(uint32_t i, uint32_t n)
-{
-    if (i >= n) {
-        atomicAdd(&g_bounds_errors, 1ull);
-        return 0u;
-    }
-    return i;
-}
-static __device__ __forceinline__ int checked_index(int i, int n)
-{
-    if (i < 0 || i >= n) {
-        atomicAdd(&g_bounds_errors, 1ull);
-        return 0;
-    }
-    return i;
-}
-#define AHS_INDEX(i, n) ::eng::checked_index((i), (n))
-// host side: this translation unit's counter on the current device (read, then
-// zeroed if reset), and a self-test launch that passes one index outside its extent
-// through the check (touching no memory)
-static __global__ void bounds_selftest_kernel()
-{
-    (void)checked_index(7, 3);
-}
-#define AHS_BOUNDS_COUNTER(name)                                                                     \
-    cudaError_t name(unsigned long long *count, int op)                                            \
-    {                                                                                              \
-        if (op == 2) {                                                                             \
-            bounds_selftest_kernel<<<1, 1>>>();                                                    \
-            cudaError_t e = cudaDeviceSynchronize();                                               \
-            if (e != cudaSuccess) return e;                                                        \
-        }                                                                                          \
-        cudaError_t e = cudaMemcpyFromSymbol(count, g_bounds_errors, sizeof(*count));              \
-        if (e != cudaSuccess || op == 0) return e;                                                 \
-        const unsigned long long zero = 0;                                                         \
-        return cudaMemcpyToSymbol(g_bounds_errors, &zero, sizeof(zero));                           \
-    }
-#else
-#define AHS_INDEX(i, n) (i)
-#define AHS_BOUNDS_COUNTER(name)                                                                     \
-    cudaError_t name(unsigned long long *count, int)                                               \
-    {                                                                                              \
-        *count = 0;                                                                                \
-        return cudaErrorNotSupported;                                                              \
-    }
-#endif
 
 // ---------------------------------------------------------------- explicit roundings
 // Arithmetic that the compiler may not contract into fused multiply-adds of its own

@@ -90,6 +90,7 @@ struct ArenaFields {
     using real = float;
     const float *base;       // the member's first plane (buffer 0, Re phi)
     uint32_t in0, out0, V;   // plane offsets of the read and write buffers, plane size
+    __device__ __forceinline__ const float *src(int f) const { return base + (in0 + (uint32_t)f * V); }
     __device__ __forceinline__ float in(int f, uint32_t o) const
     {
         return __ldg(base + (in0 + (uint32_t)f * V + AHS_INDEX(o, V)));
@@ -116,13 +117,12 @@ struct ParamFields64 {
     using real = double;
     const StepPtrs64 &P;
     uint32_t V;   // sites per plane (N^3)
-    __device__ __forceinline__ double in(int f, uint32_t o) const
+    __device__ __forceinline__ const double *src(int f) const
     {
-        o = AHS_INDEX(o, V);
-        const double *p = f == FPR ? P.pr : f == FPI ? P.pim : f == FQR ? P.qr : f == FQI ? P.qi : f == FTX ? P.tx
-                        : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : P.ez;
-        return __ldg(p + o);
+        return f == FPR ? P.pr : f == FPI ? P.pim : f == FQR ? P.qr : f == FQI ? P.qi : f == FTX ? P.tx
+             : f == FTY ? P.ty : f == FTZ ? P.tz : f == FEX ? P.ex : f == FEY ? P.ey : P.ez;
     }
+    __device__ __forceinline__ double in(int f, uint32_t o) const { return __ldg(src(f) + AHS_INDEX(o, V)); }
     __device__ __forceinline__ void out(int f, uint32_t o, double v) const
     {
         double *p = f == FPR ? P.pr1 : f == FPI ? P.pim1 : f == FQR ? P.qr1 : f == FQI ? P.qi1 : f == FTX ? P.tx1

@@ -116,8 +116,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
     const bool hasY = hasB;
     const int hyx = yRow ? hbx : T::BX, hyy = yRow ? BY : hby;
     // and the old E of the backward ring for the Gauss residual
-    uint32_t hyoff = 0, hboff = 0;
-    if (MEASURE && hasY) hyoff = (uint32_t)wrapN(x0 + hyx, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hyy, N);
+    uint32_t hboff = 0;
     if (MEASURE && hasB) hboff = (uint32_t)wrapN(x0 + hbx, N) + (uint32_t)N * (uint32_t)wrapN(y0 + hby, N);
     const uint32_t cxpoff = (uint32_t)wrapN(cx + 1, N) + (uint32_t)N * (uint32_t)cy;
     const uint32_t cypoff = (uint32_t)cx + (uint32_t)N * (uint32_t)wrapN(cy + 1, N);
@@ -221,25 +220,23 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
             const V2 p0 = pc.ph[r0], pz = pn.ph[r0];
             Syx[wi] = YxCar;
             Syy[wi] = YyCar;
-            const R tz0 = thz;
-            Syzw[wi] = link_phase_v(p0.x, p0.y, pz.x, pz.y, vz0.x, vz0.y, [&] { return tz0; });
+            Syzw[wi] = link_code(p0.x, p0.y, pz.x, pz.y, vz0.x, vz0.y);
             if (gauss) {
                 Sex[T::q(tx, ty)] = pe_cur.ex;
                 Sey[T::q(tx, ty)] = pe_cur.ey;
             }
             if (hasY) {
                 const int rh0 = T::r(hyx, hyy), wh = T::w(hyx, hyy);
-                const uint32_t ho = oc + hyoff;
                 const V2 hp = pc.ph[rh0];
                 if (yRow) {   // row BY: Y_x
                     const V2 q = pc.ph[T::r(hyx + 1, hyy)], v = pc.vx[rh0];
-                    Syx[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTX, ho); });
+                    Syx[wh] = link_code(hp.x, hp.y, q.x, q.y, v.x, v.y);
                 } else {      // column BX: Y_y
                     const V2 q = pc.ph[T::r(hyx, hyy + 1)], v = pc.vy[rh0];
-                    Syy[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTY, ho); });
+                    Syy[wh] = link_code(hp.x, hp.y, q.x, q.y, v.x, v.y);
                 }
                 const V2 q = pn.ph[rh0], v = pc.vz[rh0];
-                Syzw[wh] = link_phase_v(hp.x, hp.y, q.x, q.y, v.x, v.y, [&] { return P.in(FTZ, ho); });
+                Syzw[wh] = link_code(hp.x, hp.y, q.x, q.y, v.x, v.y);
             }
             if (gauss && hasB) {
                 if (ringRow) Sey[T::q(hbx, hby)] = eRing;
@@ -254,9 +251,8 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         if (MEASURE) {
             const V2 pn0 = pn.ph[r0], vxn = pn.vx[r0], vyn = pn.vy[r0];
             const V2 qxn = pn.ph[rxp], qyn = pn.ph[ryp];
-            const R tnx = nthx, tny = nthy;
-            YxNext = link_phase_v(pn0.x, pn0.y, qxn.x, qxn.y, vxn.x, vxn.y, [&] { return tnx; });
-            YyNext = link_phase_v(pn0.x, pn0.y, qyn.x, qyn.y, vyn.x, vyn.y, [&] { return tny; });
+            YxNext = link_code(pn0.x, pn0.y, qxn.x, qxn.y, vxn.x, vxn.y);
+            YyNext = link_code(pn0.x, pn0.y, qyn.x, qyn.y, vyn.x, vyn.y);
         }
 
         // ---- C: kick and drift of plane zz
@@ -344,20 +340,32 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
                 acc.gmax = fmax(acc.gmax, fabs(g));
                 if (!isfinite(rho) || !isfinite(L) || !isfinite(g)) acc.nf += 1;
 
-                // plaquette windings with lower corner x
+                // plaquette windings with lower corner x, from the flagged codes of
+                // their twelve distinct phases; a flagged one is recomputed in FP64
                 const int wi = T::w(tx, ty);
                 const int Yx = YxCar, Yy = YyCar, Yz = Syzw[wi];
-                const R tnx = nthx, tny = nthy;
-                const R t0x = thx, t0y = thy, t0z = thz;
-                const int wxy = wrap_from_q(Qxy.x, Qxy.y, [&](R &a, R &bb, R &c, R &d) {
-                    a = t0x; bb = P.in(FTY, oc + cxpoff); c = P.in(FTX, oc + cypoff); d = t0y; });
-                const int wxz = wrap_from_q(Qxz.x, Qxz.y, [&](R &a, R &bb, R &c, R &d) {
-                    a = t0x; bb = P.in(FTZ, oc + cxpoff); c = tnx; d = t0z; });
-                const int wyz = wrap_from_q(Qyz.x, Qyz.y, [&](R &a, R &bb, R &c, R &d) {
-                    a = t0y; bb = P.in(FTZ, oc + cypoff); c = tny; d = t0z; });
-                const int nxy = winding(Yx, Syy[T::w(tx + 1, ty)], Syx[T::w(tx, ty + 1)], Yy, wxy);
-                const int nxz = winding(Yx, Syzw[T::w(tx + 1, ty)], YxNext, Yz, wxz);
-                const int nyz = winding(Yy, Syzw[T::w(tx, ty + 1)], YyNext, Yz, wyz);
+                const int Yyx = Syy[T::w(tx + 1, ty)], Yxy = Syx[T::w(tx, ty + 1)];
+                const int Yzx = Syzw[T::w(tx + 1, ty)], Yzy = Syzw[T::w(tx, ty + 1)];
+                const int cxy = flagged_octant(Qxy.x, Qxy.y), cxz = flagged_octant(Qxz.x, Qxz.y);
+                const int cyz = flagged_octant(Qyz.x, Qyz.y);
+                int nxy, nxz, nyz;
+                if (((Yx | Yy | Yz | Yyx | Yxy | Yzx | Yzy | YxNext | YyNext | cxy | cxz | cyz) & 8) == 0) {
+                    nxy = winding_codes(Yx, Yyx, Yxy, Yy, cxy);
+                    nxz = winding_codes(Yx, Yzx, YxNext, Yz, cxz);
+                    nyz = winding_codes(Yy, Yzy, YyNext, Yz, cyz);
+                } else {
+                    const uint32_t cxypoff = (uint32_t)wrapN(cx + 1, N) + (uint32_t)N * (uint32_t)wrapN(cy + 1, N);
+                    unsigned long long codes = 0;
+                    const int cs[12] = {Yx, Yy, Yz, Yyx, Yxy, Yzx, Yzy, YxNext, YyNext, cxy, cxz, cyz};
+#pragma unroll
+                    for (int c = 0; c < 12; ++c) codes |= (unsigned long long)(cs[c] & 15) << (4 * c);
+                    const int3 w = site_windings_flagged(P.src(FPR), P.src(FPI), P.src(FTX), P.src(FTY), P.src(FTZ),
+                                                         NN * (uint32_t)N, oc + coff, oc + cxpoff, oc + cypoff,
+                                                         o1 + coff, oc + cxypoff, o1 + cxpoff, o1 + cypoff, codes);
+                    nxy = w.x;
+                    nxz = w.y;
+                    nyz = w.z;
+                }
                 acc.wind += abs(nxy) + abs(nxz) + abs(nyz);
             }
 
@@ -899,7 +907,8 @@ __global__ void __launch_bounds__(32 * BY) gauss_tiled(StepPtrs P, StepCoef k, i
     const bool valid = (x0 + tx < N) && (y0 + ty < N);
     AccT<float> acc;
     acc_zero(acc);
-    const uint32_t V = NN * (uint32_t)N;
+    const uint32_t V = NN * (uint32_t)N;   // the extent of the bounds-check build's offset checks
+    (void)V;
     float ezPrev = __ldg(P.ez + AHS_INDEX((uint32_t)wrapN(z0 - 1, N) * NN + coff, V));
     for (int zz = z0; zz < zend; ++zz) {
         const uint32_t o = (uint32_t)zz * NN;

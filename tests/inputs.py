@@ -74,6 +74,16 @@ def square_loop_phase(N: int, R: int) -> np.ndarray:
     return np.arctan2(z - c, r - R)
 
 
+def branch_cut_phase(N: int, seed: int, eps: float = 2e-6) -> np.ndarray:
+    """Phase pi (x + y) plus a uniform jitter in [-eps, eps] (N even): the phase
+    difference across every x and y link lies within 2 eps of +-pi, the branch cut
+    of arg, so the side each one lands on -- and with it most windings -- is decided
+    at the cut."""
+    rng = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(np.arange(N), np.arange(N), np.arange(N), indexing="ij")
+    return np.pi * (x + y) + rng.uniform(-eps, eps, (N, N, N))
+
+
 def with_phase(theta: np.ndarray, sigma: float = 1.0) -> np.ndarray:
     """State with phi = sigma e^{i theta} and every other field zero."""
     N = theta.shape[0]

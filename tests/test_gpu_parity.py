@@ -181,6 +181,22 @@ def test_windings_bit_exact_on_identical_snapshot(eng, orc, N, steps):
     assert n == no == obs["n_wind"]
 
 
+@pytest.mark.parametrize("N", [16, 40])
+def test_windings_at_the_branch_cut(eng, orc, N):
+    """Every x and y link phase within 4e-6 rad of +-pi: the fused measurement's
+    float32 codes are flagged at the cut and those sites' windings come from FP64
+    angles; they must equal the oracle's FP64 windings plaquette by plaquette."""
+    F = inputs.to_f32(inputs.with_phase(inputs.branch_cut_phase(N, 3))).astype(np.float64)
+    with lattice(eng, N) as lat:
+        lat.set_state(F)
+        W, n = lat.windings()
+        obs = lat.measure()
+    Wo, no = orc.windings(oparams(orc, N), F)
+    assert no > N ** 3 // 10
+    assert np.array_equal(W, Wo)
+    assert n == no == obs["n_wind"]
+
+
 def test_vortex_pair_windings(eng):
     N = 32
     F = inputs.with_phase(inputs.vortex_pair_phase(N))
