@@ -11,10 +11,12 @@ constexpr float kTwoPiF = 6.28318530717959f;
 constexpr float kInvTwoPiF = 0.159154943091895f;
 constexpr double kPiD = 3.141592653589793238;
 // A float32 complex number whose imaginary part exceeds kTie times its real part
-// has the same sign as its FP64 counterpart (float32 errors are ~1e-7 relative),
-// so its arg lies on the same side of the branch cut; closer to the cut the value
-// is recomputed in FP64 with the operations in the order of the definition.
-constexpr float kTie = 1e-4f;
+// has the same sign as its FP64 counterpart, so its arg lies on the same side of the
+// branch cut: the float32 link phase conj(p) U q is within 5e-7 |z| of the exact one
+// (link phases V within 1.5e-7, two rounded complex products), a plaquette product
+// of four link phases within 7e-7, a margin of at least 14 below kTie.  Closer to the
+// cut the value is recomputed in FP64.
+constexpr float kTie = 1e-5f;
 
 // ---------------------------------------------------------------- index checks
 // The bounds-check build of the library (-DAHS_BOUNDS_CHECK, _ahs_check.so) checks

@@ -181,12 +181,14 @@ def test_windings_bit_exact_on_identical_snapshot(eng, orc, N, steps):
     assert n == no == obs["n_wind"]
 
 
-@pytest.mark.parametrize("N", [16, 40])
-def test_windings_at_the_branch_cut(eng, orc, N):
-    """Every x and y link phase within 4e-6 rad of +-pi: the fused measurement's
-    float32 codes are flagged at the cut and those sites' windings come from FP64
-    angles; they must equal the oracle's FP64 windings plaquette by plaquette."""
-    F = inputs.to_f32(inputs.with_phase(inputs.branch_cut_phase(N, 3))).astype(np.float64)
+@pytest.mark.parametrize("N,eps", [(16, 2e-6), (40, 2e-6), (32, 5e-5)])
+def test_windings_at_the_branch_cut(eng, orc, N, eps):
+    """Every x and y link phase within 2 eps of +-pi.  With eps = 2e-6 all of them
+    are flagged (|Im z| <= 1e-5 |Re z|) and their sites' windings come from FP64
+    angles; with eps = 5e-5 most are decided by the sign of the float32 value in the
+    margin the flag leaves.  Either way the windings must equal the oracle's FP64
+    windings plaquette by plaquette."""
+    F = inputs.to_f32(inputs.with_phase(inputs.branch_cut_phase(N, 3, eps=eps))).astype(np.float64)
     with lattice(eng, N) as lat:
         lat.set_state(F)
         W, n = lat.windings()
