@@ -427,6 +427,7 @@ def run_ours(args, N):
     _abi.ahs_set_option(h, _abi.AHS_OPT_STEPS_PER_PASS, args.steps_per_pass)
     _abi.ahs_init(h, replica_seed(rank))
     shape = {"tile": [32, int(_abi.ahs_get_option(h, _abi.AHS_OPT_TILE_Y))],
+             "measure_tile": [32, int(_abi.ahs_get_option(h, _abi.AHS_OPT_MEASURE_TILE_Y))],
              "zchunk": int(_abi.ahs_get_option(h, _abi.AHS_OPT_ZCHUNK))}
 
     barrier = group.barrier

@@ -76,7 +76,7 @@ enum {
     AHS_OPT_WRAP_THETA = 4,    /* 1: keep theta in (-pi, pi] after each drift; default 0       */
     AHS_OPT_PROFILE = 5,       /* 1: time every step-kernel launch with CUDA events            */
     AHS_OPT_N = 6,             /* lattice side (read only)                                     */
-    AHS_OPT_TILE_Y = 7,        /* step-kernel tile height: 8 or 16 rows of 32 sites; 0 = auto   */
+    AHS_OPT_TILE_Y = 7,        /* plain-step tile height: 8 or 16 rows of 32 sites; 0 = auto    */
     AHS_OPT_ZCHUNK = 8,        /* z planes one CTA marches through, 1..N; 0 = auto            */
     AHS_OPT_GRAPH = 9,         /* batches: 1 = replay each measurement period as a CUDA graph  */
     AHS_OPT_PRECISION = 10,    /* AHS_PREC_*; default FP32                                     */
@@ -85,7 +85,9 @@ enum {
     AHS_OPT_MOMENTA_IN_PLACE = 12, /* 1: keep one copy of Pi and E and update it in place */
     AHS_OPT_CORE_GROWTH_S = 13,   /* s of the core-growth period (see below); default 0    */
     AHS_OPT_CORE_GROWTH_TAU = 14, /* end eta_cg of the period; <= eta0 (default): none     */
-    AHS_OPT_STEPS_PER_PASS = 15   /* 1 (default) or 2: temporal blocking, see below          */
+    AHS_OPT_STEPS_PER_PASS = 15,  /* 1 (default) or 2: temporal blocking, see below          */
+    AHS_OPT_MEASURE_TILE_Y = 16   /* tile height of measuring steps (and of ahs_measure): 4, 8
+                                     or 16 rows of 32 sites; 0 = auto (4; FP64 precision: 8) */
 };
 
 /* AHS_OPT_STEPS_PER_PASS = 2 (float32 precision with double-buffered momenta only).
@@ -320,7 +322,8 @@ int ahs_batch_set_stream(ahs_batch_t *b, void *cuda_stream);
 void ahs_batch_destroy(ahs_batch_t *b);
 
 /* ahs_autotune -- choose AHS_OPT_TILE_Y and AHS_OPT_ZCHUNK of a single lattice by
- * timing its plain step (CUDA events, the state is not changed); needs fields. */
+ * timing its plain step, then AHS_OPT_MEASURE_TILE_Y at that z-chunk by timing
+ * measure-only launches (CUDA events, the state is not changed); needs fields. */
 int ahs_autotune(ahs_t *h);
 
 /* ahs_measure_noalloc -- the measurement of ahs_measure on fields the caller
@@ -345,7 +348,12 @@ int ahs_autotune(ahs_t *h);
  * address (cudaGetSymbolAddress) with that device current and keeps it for the
  * life of the process; make that first call before any stream capture.  The kept
  * address is not valid after cudaDeviceReset (or any other re-creation of the
- * device's primary context): do not call this entry point after one.  Returns AHS_EINVAL for N outside [4, 1600] (a
+ * device's primary context): do not call this entry point after one.  The launch
+ * takes the automatic measuring shape of ahs_measure (32 x 4 tiles) with its
+ * z-chunks lengthened until the CTAs fit the scratch rows, or 32 x 8 tiles where
+ * even one chunk of 4-row tiles would not fit (N > 1440): the record equals that
+ * of ahs_measure at the same launch shape, and at another one up to the grouping
+ * of the FP64 sums.  Returns AHS_EINVAL for N outside [4, 1600] (a
  * lattice whose CTAs cannot fit the scratch is rejected the same way), bad
  * parameters or NULL buffers, AHS_ECUDA if a launch fails. */
 #define AHS_NOALLOC_MAX_ROWS 16384

@@ -124,7 +124,7 @@ class Lattice:
     _SAVED_OPTIONS = ("AHS_OPT_STEP", "AHS_OPT_ALPHA", "AHS_OPT_TAU0", "AHS_OPT_WRAP_THETA",
                       "AHS_OPT_MEASURE_EVERY", "AHS_OPT_PRECISION", "AHS_OPT_COOLING",
                       "AHS_OPT_MOMENTA_IN_PLACE", "AHS_OPT_CORE_GROWTH_S", "AHS_OPT_CORE_GROWTH_TAU",
-                      "AHS_OPT_TILE_Y", "AHS_OPT_ZCHUNK", "AHS_OPT_STEPS_PER_PASS")
+                      "AHS_OPT_TILE_Y", "AHS_OPT_ZCHUNK", "AHS_OPT_STEPS_PER_PASS", "AHS_OPT_MEASURE_TILE_Y")
 
     def save(self, path: str):
         """Write a restart file (numpy .npz): the fields at the current time level in

@@ -23,7 +23,7 @@ AHS_PREC_FP32, AHS_PREC_FP32_COMPENSATED, AHS_PREC_FP64 = 0, 1, 2
 (AHS_OPT_MEASURE_EVERY, AHS_OPT_ALPHA, AHS_OPT_TAU0, AHS_OPT_STEP, AHS_OPT_WRAP_THETA,
  AHS_OPT_PROFILE, AHS_OPT_N, AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK, AHS_OPT_GRAPH, AHS_OPT_PRECISION,
  AHS_OPT_COOLING, AHS_OPT_MOMENTA_IN_PLACE, AHS_OPT_CORE_GROWTH_S, AHS_OPT_CORE_GROWTH_TAU,
- AHS_OPT_STEPS_PER_PASS) = range(16)
+ AHS_OPT_STEPS_PER_PASS, AHS_OPT_MEASURE_TILE_Y) = range(17)
 AHS_KERNEL_STEP, AHS_KERNEL_STEP_MEASURE, AHS_KERNEL_STEP_PAIR = 0, 1, 2
 
 # every symbol include/ahs.h declares

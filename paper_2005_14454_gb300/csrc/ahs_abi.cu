@@ -71,6 +71,7 @@ struct ahs : eng::LatticeParams {
     double *partials = nullptr;      // nblocks * NQ
     int nblocks = 0;                 // capacity of partials in rows
     int tile_y = 0, zchunk = 0;      // launch-shape overrides (0: automatic)
+    int measure_tile_y = 0;          // tile height of measuring launches (0: automatic)
     ahs_obs_t *rec_dev = nullptr;    // device records of one ahs_step call
     int rec_cap = 0;
     ahs_obs_t *rec_host = nullptr;   // pinned staging
@@ -135,24 +136,27 @@ StepPtrs64 pointers64(const ahs_t *h)
     return p;
 }
 
-// CTAs (rows of partials) of the current step launch
-int launch_blocks(const ahs_t *h)
+// the launch shape of a plain or a measuring step (FP64: 8-row tiles for both)
+StepShape shape_of(const ahs_t *h, bool measure)
 {
-    if (h->precision == AHS_PREC_FP64) return step_shape(h->N, 8, h->zchunk).blocks;
-    return step_shape(h->N, h->tile_y, h->zchunk).blocks;
+    if (h->precision == AHS_PREC_FP64) return step_shape(h->N, 8, h->zchunk);
+    return measure ? measure_shape(h->N, h->measure_tile_y, h->zchunk) : step_shape(h->N, h->tile_y, h->zchunk);
 }
+
+// CTAs (rows of partials) of the current measuring launch
+int launch_blocks(const ahs_t *h) { return shape_of(h, true).blocks; }
 
 // one step launch (measure: diagnostics into the partials; store: write n+1;
 // gauss false: the Gauss residual's slots were written by launch_gauss)
 cudaError_t launch_current(const ahs_t *h, bool measure, bool store, bool gauss = true)
 {
     if (h->precision == AHS_PREC_FP64)
-        return launch_step64(pointers64(h), coefficients64(h, h->n), h->N, step_shape(h->N, 8, h->zchunk), measure,
-                             store, h->partials, h->stream);
+        return launch_step64(pointers64(h), coefficients64(h, h->n), h->N, shape_of(h, measure), measure, store,
+                             h->partials, h->stream);
     StepCoef k = coefficients(h, h->n);
     k.gauss = gauss ? 1 : 0;
-    return launch_step(pointers(h), k, h->N, step_shape(h->N, h->tile_y, h->zchunk), measure, store, h->partials,
-                       h->stream, h->precision == AHS_PREC_FP32_COMPENSATED);
+    return launch_step(pointers(h), k, h->N, shape_of(h, measure), measure, store, h->partials, h->stream,
+                       h->precision == AHS_PREC_FP32_COMPENSATED);
 }
 
 // the storage layout of the handle's precision and storage mode; frees any field
@@ -293,7 +297,7 @@ ahs_t *ahs_create(int N, double dx, double dt, double lambda0, double e0, double
         return nullptr;
     }
     reset_fields(h);
-    h->nblocks = step_shape(N, 0, 0).blocks;
+    h->nblocks = measure_shape(N, 0, 0).blocks;
     cudaError_t e = cudaMalloc(&h->partials, sizeof(double) * NQ * (size_t)h->nblocks);
     if (e != cudaSuccess) {
         fail(AHS_ENOMEM, "cudaMalloc(partials): %s", cudaGetErrorString(e));
@@ -391,6 +395,10 @@ int ahs_set_option(ahs_t *h, int key, double v)
         if (v != 0 && v != 8 && v != 16) return fail(AHS_EINVAL, "tile_y must be 0, 8 or 16");
         h->tile_y = (int)v;
         return ok();
+    case AHS_OPT_MEASURE_TILE_Y:
+        if (v != 0 && v != 4 && v != 8 && v != 16) return fail(AHS_EINVAL, "measure_tile_y must be 0, 4, 8 or 16");
+        h->measure_tile_y = (int)v;
+        return ok();
     case AHS_OPT_ZCHUNK:
         if (!(v >= 0) || v > h->N || v != std::floor(v)) return fail(AHS_EINVAL, "zchunk must be an integer in [0, N]");
         h->zchunk = (int)v;
@@ -462,7 +470,8 @@ int ahs_get_option(ahs_t *h, int key, double *v)
     case AHS_OPT_CORE_GROWTH_S: *v = h->s_cg; break;
     case AHS_OPT_CORE_GROWTH_TAU: *v = h->tau_cg; break;
     case AHS_OPT_STEPS_PER_PASS: *v = h->steps_per_pass; break;
-    case AHS_OPT_TILE_Y: *v = h->precision == AHS_PREC_FP64 ? 8 : step_shape(h->N, h->tile_y, h->zchunk).by; break;
+    case AHS_OPT_TILE_Y: *v = shape_of(h, false).by; break;
+    case AHS_OPT_MEASURE_TILE_Y: *v = shape_of(h, true).by; break;
     case AHS_OPT_ZCHUNK: *v = step_shape(h->N, h->tile_y, h->zchunk).dz; break;
     default: return fail(AHS_EINVAL, "unknown option %d", key);
     }
@@ -511,8 +520,7 @@ int ahs_step(ahs_t *h, int nsteps)
         if (meas && h->inplace) {
             // the Gauss residual reads neighbours' old E, which an in-place step
             // overwrites: it goes first, into the measuring launch's partial rows
-            CU(launch_gauss(pointers(h), coefficients(h, h->n), h->N, step_shape(h->N, h->tile_y, h->zchunk),
-                            h->partials, h->stream));
+            CU(launch_gauss(pointers(h), coefficients(h, h->n), h->N, shape_of(h, true), h->partials, h->stream));
             CU(launch_current(h, true, true, false));
         } else {
             CU(launch_current(h, meas, true));
@@ -703,8 +711,33 @@ int ahs_autotune(ahs_t *h)
                 best_dz = dz;
             }
         }
+    // then the measuring step's tile height at that z-chunk, by timing measure-only
+    // launches (they write only the partial rows)
+    StepCoef km = k;
+    km.gauss = 1;
+    double mbest = 1e300;
+    int best_mby = 4;
+    for (int mby : {4, 8, 16}) {
+        const StepShape sh = measure_shape(h->N, mby, best_dz);
+        if (int r = ensure_partials(h, sh.blocks)) return r;
+        CU(launch_step(p, km, h->N, sh, true, false, h->partials, h->stream, comp));   // warm-up
+        float tot = 0.f, ms = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            CU(cudaEventRecord(e0, h->stream));
+            CU(launch_step(p, km, h->N, sh, true, false, h->partials, h->stream, comp));
+            CU(cudaEventRecord(e1, h->stream));
+            CU(cudaEventSynchronize(e1));
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            tot += ms;
+        }
+        if (tot < mbest) {
+            mbest = tot;
+            best_mby = mby;
+        }
+    }
     h->tile_y = best_by;
     h->zchunk = best_dz;
+    h->measure_tile_y = best_mby;
     return ok();
 }
 

@@ -83,12 +83,15 @@ struct ObsScalars {
 
 // Launchers (ahs_kernels.cu).  All take the stream they run on.
 cudaError_t launch_init(float *pr, float *pim, int N, uint64_t seed, double sigma, cudaStream_t st);
-// Launch shape of the z-marching step kernel: tile height (8 or 16 rows of 32
+// Launch shape of the z-marching step kernel: tile height (4, 8 or 16 rows of 32
 // sites), z-chunk per CTA, and the number of CTAs (= rows of measurement partials).
 struct StepShape {
     int by, dz, blocks;
 };
 StepShape step_shape(int N, int tile_y, int zchunk);   // tile_y/zchunk 0: automatic
+// the shape of a measuring launch (and of the Gauss pass that goes with it): tile
+// height 4, 8 or 16 (0: automatic, 4)
+StepShape measure_shape(int N, int tile_y, int zchunk);
 cudaError_t launch_step(const StepPtrs &p, const StepCoef &k, int N, const StepShape &sh, bool measure, bool store,
                         double *partials, cudaStream_t st, bool compensated = false);
 // FP64 precision: the tiled step in double, 8-row tiles (sh.by must be 8)

@@ -69,17 +69,24 @@ extern "C" int ahs_measure_noalloc(int N, double dx, double dt, double lambda0, 
         return report_error(AHS_EINVAL, "invalid lattice parameters");
     if (!fields || !out) return report_error(AHS_EINVAL, "null device buffer");
 
-    // launch shape: the automatic one, with longer z marches if its CTAs would not
-    // all fit the static scratch
-    StepShape sh = step_shape(N, 8, 0);
-    if (sh.blocks > AHS_NOALLOC_MAX_ROWS) {
-        const int tiles = ((N + 31) / 32) * ((N + 7) / 8);
-        const int chunks = AHS_NOALLOC_MAX_ROWS / tiles;
-        if (chunks < 1) return report_error(AHS_EINVAL, "lattice too large for the static measurement scratch");
-        sh = step_shape(N, 8, (N + chunks - 1) / chunks);
-        if (sh.blocks > AHS_NOALLOC_MAX_ROWS)
-            return report_error(AHS_EINVAL, "lattice too large for the static measurement scratch");
+    // launch shape: the automatic measuring one (4-row tiles), with longer z marches
+    // if its CTAs would not all fit the static scratch, else 8-row tiles
+    StepShape sh{};
+    bool fits = false;
+    for (int by : {4, 8}) {
+        sh = measure_shape(N, by, 0);
+        if (sh.blocks > AHS_NOALLOC_MAX_ROWS) {
+            const int tiles = ((N + 31) / 32) * ((N + by - 1) / by);
+            const int chunks = AHS_NOALLOC_MAX_ROWS / tiles;
+            if (chunks < 1) continue;
+            sh = measure_shape(N, by, (N + chunks - 1) / chunks);
+        }
+        if (sh.blocks <= AHS_NOALLOC_MAX_ROWS) {
+            fits = true;
+            break;
+        }
     }
+    if (!fits) return report_error(AHS_EINVAL, "lattice too large for the static measurement scratch");
     void *scratch = nullptr;
     if (int r = scratch_address(&scratch)) return r;
 

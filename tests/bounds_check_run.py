@@ -45,7 +45,8 @@ def main():
     paths = 0
     for N in SIDES:
         era = 1 + N % 2
-        for opts in ({}, {"AHS_OPT_TILE_Y": 16}, {"AHS_OPT_ZCHUNK": 3}, {"AHS_OPT_ZCHUNK": N},
+        for opts in ({}, {"AHS_OPT_TILE_Y": 16}, {"AHS_OPT_MEASURE_TILE_Y": 8}, {"AHS_OPT_MEASURE_TILE_Y": 16},
+                     {"AHS_OPT_ZCHUNK": 3}, {"AHS_OPT_ZCHUNK": N},
                      {"momenta_in_place": True}, {"precision": "fp32c"}, {"precision": "fp64"},
                      {"steps_per_pass": 2}, {"steps_per_pass": 2, "AHS_OPT_ZCHUNK": 2}):
             run_lattice(N, era, **dict(opts))

@@ -47,10 +47,10 @@ def test_fields_and_records_bit_identical_to_double_buffering(eng, N, era, s, st
 
 
 def test_perturbed_gauge_fields_and_launch_shapes(eng):
-    from paper_2005_14454_gb300._abi import AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK
+    from paper_2005_14454_gb300._abi import AHS_OPT_MEASURE_TILE_Y, AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK
     N = 40
     F = inputs.to_f32(inputs.perturbed_state(N, seed=11))
-    for shape in ({}, {AHS_OPT_TILE_Y: 16, AHS_OPT_ZCHUNK: 7}):
+    for shape in ({}, {AHS_OPT_TILE_Y: 16, AHS_OPT_ZCHUNK: 7}, {AHS_OPT_MEASURE_TILE_Y: 8, AHS_OPT_ZCHUNK: 5}):
         (F0, R0, _), (F1, R1, _) = run_pair(eng, N, 15, start=F, shape=shape)
         assert np.array_equal(F0, F1)
         assert R0 == R1

@@ -100,13 +100,14 @@ def test_ten_steps_match_oracle(eng, orc, N, era, s):
 @pytest.mark.parametrize("N", [20, 40, 64])
 def test_launch_shapes_give_identical_fields(eng, N):
     # every link phase and plaquette is computed by the same arithmetic whatever the
-    # tile height and z-chunk, so the fields agree bit for bit; the reductions
-    # differ only in grouping
-    from paper_2005_14454_gb300._abi import AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK
+    # tile heights (plain and measuring steps) and z-chunk, so the fields agree bit
+    # for bit; the reductions differ only in grouping
+    from paper_2005_14454_gb300._abi import AHS_OPT_MEASURE_TILE_Y, AHS_OPT_TILE_Y, AHS_OPT_ZCHUNK
     outs, recs = [], []
-    for by, dz in [(8, 0), (16, 0), (8, 5), (16, 3), (8, N), (16, 1)]:
+    for by, mby, dz in [(8, 0, 0), (16, 8, 0), (8, 16, 5), (16, 4, 3), (8, 8, N), (16, 4, 1), (8, 4, 2)]:
         with lattice(eng, N, measure_every=3) as lat:
             lat.set_option(AHS_OPT_TILE_Y, by)
+            lat.set_option(AHS_OPT_MEASURE_TILE_Y, mby)
             lat.set_option(AHS_OPT_ZCHUNK, dz)
             lat.init(5)
             lat.step(7)
@@ -119,6 +120,27 @@ def test_launch_shapes_give_identical_fields(eng, N):
             assert a["n_wind"] == b["n_wind"]
             assert a["e_total"] == pytest.approx(b["e_total"], rel=1e-6)
             assert a["lagrangian"] == pytest.approx(b["lagrangian"], rel=1e-5)
+
+
+def test_measure_tile_height_option(eng):
+    """AHS_OPT_MEASURE_TILE_Y: 4-row tiles by default (8 in FP64 precision), 4, 8 or
+    16 when set, anything else rejected; ahs_autotune picks one of the three."""
+    from paper_2005_14454_gb300 import _abi
+    L = _abi.lib()
+    key = _abi.AHS_OPT_MEASURE_TILE_Y
+    with lattice(eng, 24) as lat:
+        assert int(_abi.ahs_get_option(lat.h, key)) == 4
+        for bad in (1, 2, 12, 32, -4, 4.5):
+            assert L.ahs_set_option(lat.h, key, bad) == _abi.AHS_EINVAL
+        assert b"measure_tile_y" in L.ahs_last_error_message()
+        for v in (16, 8, 4):
+            lat.set_option(key, v)
+            assert int(_abi.ahs_get_option(lat.h, key)) == v
+        lat.init(3)
+        lat.autotune()
+        assert int(_abi.ahs_get_option(lat.h, key)) in (4, 8, 16)
+        lat.set_option(_abi.AHS_OPT_PRECISION, _abi.AHS_PREC_FP64)
+        assert int(_abi.ahs_get_option(lat.h, key)) == 8
 
 
 def test_perturbed_state_with_gauge_fields(eng, orc):
@@ -351,18 +373,19 @@ def check_sites(orc, before, after, n):
 
 def test_full_size_sampled_sites(eng, orc):
     """1024^3 in the launch configuration the benchmark times: a plain step (the
-    paired kernel) and a measuring step (the fused measurement kernel, 32 x 8 tiles,
-    192-plane z-chunks, 24576 rows of partial sums), each checked at sampled sites
+    paired kernel) and a measuring step (the fused measurement kernel, 32 x 4 tiles,
+    192-plane z-chunks, 49152 rows of partial sums), each checked at sampled sites
     against the oracle run on the 5^3 periodic neighbourhood of each site (the update
     of a site reads only its nearest and next-nearest neighbours).  The record of the
     measuring step is checked by properties that hold at any size: it equals
     ahs_measure at the same launch shape bit for bit, its winding count equals the
-    sum of |W| of the separate winding kernel, and a measurement at another z-chunk
-    (64 planes, 65536 rows) agrees up to the grouping of the sums."""
+    sum of |W| of the separate winding kernel, and measurements at another z-chunk
+    (64 planes, 131072 rows) and with 8-row tiles (24576 rows) agree up to the
+    grouping of the sums."""
     N = 1024
     sites = sampled_sites(N, 12, 0)
     from paper_2005_14454_gb300 import AHS_FIELD_ALL
-    from paper_2005_14454_gb300._abi import AHS_OPT_ZCHUNK
+    from paper_2005_14454_gb300._abi import AHS_OPT_MEASURE_TILE_Y, AHS_OPT_ZCHUNK
 
     def boxes(lat, w):
         o = -(w // 2)
@@ -377,7 +400,8 @@ def test_full_size_sampled_sites(eng, orc):
         check_sites(orc, before, [b[:, 0, 0, 0] for b in boxes(lat, 1)], 3)
         lat.step(6)
         assert lat.n == 10
-        assert int(__import__("paper_2005_14454_gb300")._abi.ahs_get_option(lat.h, AHS_OPT_ZCHUNK)) == 192
+        get = __import__("paper_2005_14454_gb300")._abi.ahs_get_option
+        assert int(get(lat.h, AHS_OPT_ZCHUNK)) == 192 and int(get(lat.h, AHS_OPT_MEASURE_TILE_Y)) == 4
         lat.records()
         before = boxes(lat, 5)
         standalone = lat.measure()
@@ -386,24 +410,28 @@ def test_full_size_sampled_sites(eng, orc):
         lat.set_option(AHS_OPT_ZCHUNK, 64)
         other = lat.measure()
         lat.set_option(AHS_OPT_ZCHUNK, 0)
+        lat.set_option(AHS_OPT_MEASURE_TILE_Y, 8)
+        rows8 = lat.measure()
+        lat.set_option(AHS_OPT_MEASURE_TILE_Y, 0)
         lat.step(1)                                # n = 10: measuring step
         rec = lat.records()
         check_sites(orc, before, [b[:, 0, 0, 0] for b in boxes(lat, 1)], 10)
     assert [r["step"] for r in rec] == [10]
     assert rec[0] == standalone
-    assert rec[0]["n_wind"] == n_wind == other["n_wind"] > 0
-    assert rec[0]["gauss_max"] == other["gauss_max"]
+    assert rec[0]["n_wind"] == n_wind == other["n_wind"] == rows8["n_wind"] > 0
+    assert rec[0]["gauss_max"] == other["gauss_max"] == rows8["gauss_max"]
     assert rec[0]["nonfinite"] == 0
-    for k in SUMS:
-        assert rec[0][k] == pytest.approx(other[k], rel=1e-5), k
-    for k in SIGNED:
-        assert rec[0][k] == pytest.approx(other[k], rel=2e-4), k
+    for alt in (other, rows8):
+        for k in SUMS:
+            assert rec[0][k] == pytest.approx(alt[k], rel=1e-5), k
+        for k in SIGNED:
+            assert rec[0][k] == pytest.approx(alt[k], rel=2e-4), k
 
 
 def test_measure_at_benchmark_zchunk_matches_oracle(eng, orc):
     """The fused measurement at the z-chunk the 1024^3 benchmark uses (192 planes),
-    on a 640^3 lattice (three full chunks and a ragged one of 64; 6400 rows of
-    partial sums) against the oracle's measurement of the same snapshot: windings
+    on a 640^3 lattice (three full chunks and a ragged one of 64; 32 x 4 tiles,
+    12800 rows of partial sums) against the oracle's measurement of the same snapshot: windings
     bit-exact, sums and ratios to the tolerances of the identical-snapshot test."""
     from paper_2005_14454_gb300._abi import AHS_OPT_ZCHUNK
     N, steps = 640, 10

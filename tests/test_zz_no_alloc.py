@@ -102,9 +102,9 @@ def test_noalloc_matches_oracle_and_measure_on_calls_in_a_row(orc):
 
 
 def test_noalloc_rechunked_launch_at_1024():
-    """At 1024^3 the automatic launch (32 x 8 tiles, 192-plane z-chunks) has 24576
-    CTAs, more than the 16384 rows of the static scratch, so the entry point
-    lengthens the z-chunks (256 planes, 16384 CTAs).  The record equals that of
+    """At 1024^3 the automatic measuring launch (32 x 4 tiles, 192-plane z-chunks)
+    has 49152 CTAs, more than the 16384 rows of the static scratch, so the entry
+    point lengthens the z-chunks (512 planes, 16384 CTAs).  The record equals that of
     ahs_measure at its own launch shape up to the grouping of the sums: windings
     and the largest Gauss residual exactly, sums to the parity tolerances."""
     import paper_2005_14454_gb300 as pkg
