@@ -303,7 +303,8 @@ int ahs_batch_set_fields(ahs_batch_t *b, int m, int which, const void *host_src,
 /* current time level and last step of member m */
 int ahs_batch_step_info(ahs_batch_t *b, int m, int64_t *n, int64_t *n_end);
 /* options: MEASURE_EVERY (change only on a multiple of the old cadence), ALPHA,
- * TAU0, WRAP_THETA, PROFILE, TILE_Y (8/16), ZCHUNK (all members; 0 = auto), GRAPH */
+ * TAU0, WRAP_THETA, PROFILE, TILE_Y (8/16: one-site plain tiles of odd sides),
+ * MEASURE_TILE_Y (4/8/16, 0 = 4: measuring tiles), ZCHUNK (all members; 0 = auto), GRAPH */
 int ahs_batch_set_option(ahs_batch_t *b, int key, double value);
 int ahs_batch_get_option(ahs_batch_t *b, int key, double *value);
 /* z-chunk member m currently uses */

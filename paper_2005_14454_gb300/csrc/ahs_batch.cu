@@ -7,7 +7,7 @@
 // fields are bit-identical to a single-lattice run of the same seed and launch
 // shape.  Members stop at their own last step (half light-crossing, Sec. 2, by
 // default) while the others continue.  Three work lists: the measuring steps of
-// all members on one-site 32 x by tiles (their partial rows are the rows of a
+// all members on one-site 32 x mby tiles (their partial rows are the rows of a
 // single lattice's measuring launch, so the records match too); the plain steps
 // of members of even side on paired 64 x 8 tiles (the single lattice's plain step
 // on even N); the plain steps of members of odd side on one-site tiles.
@@ -50,7 +50,8 @@ struct ahs_batch {
     std::vector<int64_t> n_end;
     std::vector<size_t> off;      // float offset of each member in the arena
     std::vector<int> dz;          // z-chunk per member
-    int by = 8;
+    int by = 8;                   // one-site plain tiles (odd sides)
+    int mby = 4;                  // measuring tiles
     int measure_every = 10;
     int use_graph = 1;
     int profile = 0;
@@ -221,7 +222,7 @@ int build_tiles(ahs_batch_t *b)
     }
     std::vector<BatchTile> tm, tp, to;
     std::vector<int> lm, lp, lo;
-    make([](int) { return true; }, 32, b->by, tm, lm, true);
+    make([](int) { return true; }, 32, b->mby, tm, lm, true);
     make([&](int m) { return b->prm[m].N % 2 == 0; }, 64, 8, tp, lp, false);
     make([&](int m) { return b->prm[m].N % 2 != 0; }, 32, b->by, to, lo, false);
     BatchMember *keep_members = nullptr;
@@ -242,7 +243,7 @@ int build_tiles(ahs_batch_t *b)
         BCU(cudaMalloc(&b->d_partials, sizeof(double) * NQ * (size_t)b->ntiles));
         b->rows_cap = b->ntiles;
     }
-    b->grid_meas = std::min(batch_grid(b->by, true), b->ntiles);
+    b->grid_meas = std::min(batch_grid(b->mby, true), b->ntiles);
     b->grid_plain = b->notiles ? std::min(batch_grid(b->by, false), b->notiles) : 0;
     b->grid_pair = b->nptiles ? std::min(batch_pair_grid(), b->nptiles) : 0;
     if (b->grid_meas < 1 || (b->notiles && b->grid_plain < 1) || (b->nptiles && b->grid_pair < 1))
@@ -318,7 +319,7 @@ cudaError_t enqueue_steps(ahs_batch_t *b, int64_t n0, int len, cudaStream_t st)
     const int G = b->measure_every;
     for (int d = 0; d < len; ++d) {
         const bool meas = G > 0 && ((n0 + d) % G == 0);
-        cudaError_t e = meas ? launch_batch_step(L, b->by, d, true, b->grid_meas, st) : enqueue_plain(b, d, st);
+        cudaError_t e = meas ? launch_batch_step(L, b->mby, d, true, b->grid_meas, st) : enqueue_plain(b, d, st);
         if (e != cudaSuccess) return e;
         if (meas) {
             e = launch_batch_reduce(b->d_partials, b->d_members, b->count, b->d_obs, b->obs_stride, b->d_counter, d, G,
@@ -601,7 +602,7 @@ int ahs_batch_measure(ahs_batch_t *b, int m, ahs_obs_t *out)
     BCU(cudaSetDevice(b->device));
     const LatticeParams &P = b->prm[m];
     const int64_t t = b->member_time(m);
-    const StepShape sh = step_shape(P.N, b->by, b->dz[m]);
+    const StepShape sh = measure_shape(P.N, b->mby, b->dz[m]);
     BCU(cudaStreamSynchronize(b->stream));
     if (sh.blocks > b->mpart_rows) {
         cudaFree(b->d_mpart);
@@ -680,6 +681,11 @@ int ahs_batch_set_option(ahs_batch_t *b, int key, double v)
         b->by = (int)v;
         b->tiles_dirty = true;
         return report_ok();
+    case AHS_OPT_MEASURE_TILE_Y:
+        if (v != 0 && v != 4 && v != 8 && v != 16) return bfail(AHS_EINVAL, "measure_tile_y must be 0, 4, 8 or 16");
+        b->mby = v == 0 ? 4 : (int)v;
+        b->tiles_dirty = true;
+        return report_ok();
     case AHS_OPT_ZCHUNK:
         if (!(v >= 0) || v > 1600 || v != std::floor(v)) return bfail(AHS_EINVAL, "zchunk must be an integer in [0, 1600]");
         for (int m = 0; m < b->count; ++m) b->dz[m] = step_shape(b->prm[m].N, b->by, (int)v).dz;
@@ -709,6 +715,7 @@ int ahs_batch_get_option(ahs_batch_t *b, int key, double *v)
     case AHS_OPT_CORE_GROWTH_S: *v = b->prm[0].s_cg; break;
     case AHS_OPT_CORE_GROWTH_TAU: *v = b->prm[0].tau_cg; break;
     case AHS_OPT_TILE_Y: *v = b->by; break;
+    case AHS_OPT_MEASURE_TILE_Y: *v = b->mby; break;
     case AHS_OPT_GRAPH: *v = b->use_graph; break;
     case AHS_OPT_STEP: *v = (double)b->n; break;
     default: return bfail(AHS_EINVAL, "unknown option");

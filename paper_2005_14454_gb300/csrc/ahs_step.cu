@@ -983,6 +983,7 @@ StepShape measure_shape(int N, int tile_y, int zchunk)
 
 int batch_grid(int by, bool measure)
 {
+    if (by == 4) return measure ? batch_occupancy<4, true>() : 0;   // 4-row tiles: measuring steps only
     if (by == 16) return measure ? batch_occupancy<16, true>() : batch_occupancy<16, false>();
     return measure ? batch_occupancy<8, true>() : batch_occupancy<8, false>();
 }
@@ -1001,6 +1002,7 @@ cudaError_t launch_batch_pair_step(const BatchLaunch &L, int dn, int grid, cudaS
 cudaError_t launch_batch_step(const BatchLaunch &L, int by, int dn, bool measure, int grid, cudaStream_t st)
 {
     if (grid < 1) return cudaErrorInvalidConfiguration;
+    if (by == 4) return measure ? launch_batch_variant<4, true>(L, dn, grid, st) : cudaErrorInvalidValue;
     if (by == 16) return measure ? launch_batch_variant<16, true>(L, dn, grid, st) : launch_batch_variant<16, false>(L, dn, grid, st);
     return measure ? launch_batch_variant<8, true>(L, dn, grid, st) : launch_batch_variant<8, false>(L, dn, grid, st);
 }

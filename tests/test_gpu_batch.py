@@ -55,6 +55,35 @@ def test_batch_equals_single_runs(pkg, graph, members):
             assert got == rec
 
 
+def test_batch_measuring_tile_height(pkg):
+    """Measuring steps on 4-row tiles (the default) or 8- and 16-row ones: the fields
+    are the same bit for bit, the records those of single lattices of the same
+    measuring height, and other heights are rejected."""
+    from paper_2005_14454_gb300 import _abi
+    key = _abi.AHS_OPT_MEASURE_TILE_Y
+    members = MIXED[:4]
+    with make_batch(pkg, members=members) as a:
+        assert int(_abi.ahs_batch_get_option(a.b, key)) == 4
+        for bad in (2, 12, -1, 4.5):
+            assert _abi.lib().ahs_batch_set_option(a.b, key, bad) == _abi.AHS_EINVAL
+        a.init()
+        a.run()
+        ref = [a.state(i) for i in range(len(members))]
+    for mby in (8, 16):
+        with make_batch(pkg, members=members) as b:
+            b.set_option(key, mby)
+            assert int(_abi.ahs_batch_get_option(b.b, key)) == mby
+            b.init()
+            b.run()
+            for i, (N, era, seed, end) in enumerate(members):
+                assert np.array_equal(b.state(i), ref[i]), (mby, i)
+                with pkg.Lattice(N, era=era, measure_every=5, **PARAMS) as lat:
+                    lat.set_option(key, mby)
+                    lat.init(seed)
+                    lat.step(end)
+                    assert b.records(i) == lat.records(), (mby, i)
+
+
 def test_batch_runs_in_pieces(pkg):
     # uneven run lengths: graph periods and single steps interleave
     with make_batch(pkg) as b1, make_batch(pkg) as b2:
