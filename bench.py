@@ -423,6 +423,7 @@ def run_ours(args, N):
         _abi.ahs_set_option(h, _abi.AHS_OPT_MOMENTA_IN_PLACE, 1)
     _abi.ahs_set_option(h, _abi.AHS_OPT_MEASURE_EVERY, PERIOD)
     _abi.ahs_set_option(h, _abi.AHS_OPT_TILE_Y, args.tile_y)
+    _abi.ahs_set_option(h, _abi.AHS_OPT_MEASURE_TILE_Y, args.measure_tile_y)
     _abi.ahs_set_option(h, _abi.AHS_OPT_ZCHUNK, args.zchunk)
     _abi.ahs_set_option(h, _abi.AHS_OPT_STEPS_PER_PASS, args.steps_per_pass)
     _abi.ahs_init(h, replica_seed(rank))
@@ -548,6 +549,7 @@ def main():
     ap.add_argument("--size", type=int, default=1024)
     ap.add_argument("--ref-size", type=int, default=128)
     ap.add_argument("--tile-y", type=int, default=0, help="step-kernel tile height (8, 16; 0 = auto)")
+    ap.add_argument("--measure-tile-y", type=int, default=0, help="measuring-step tile height (4, 8, 16; 0 = auto)")
     ap.add_argument("--zchunk", type=int, default=0, help="z planes per CTA (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
