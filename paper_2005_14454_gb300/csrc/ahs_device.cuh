@@ -266,11 +266,12 @@ static __device__ __forceinline__ int link_code(R pr, R pi, R qr, R qi, R vc, R 
     return flagged_octant(zr, zi);
 }
 
-// winding() of five flagged codes (flags ignored: the caller checks them); the
-// offsets of 4 cancel in c1 + c2 - c3 - c4 and one is left from ca
+// winding() of five codes without flags (the caller has checked that none is set,
+// so each is its octant + 4); the offsets of 4 cancel in c1 + c2 - c3 - c4 and one
+// is left from ca
 static __device__ __forceinline__ int winding_codes(int c1, int c2, int c3, int c4, int ca)
 {
-    const int t = (c1 & 7) + (c2 & 7) - (c3 & 7) - (c4 & 7) + (ca & 7) - 4;
+    const int t = c1 + c2 - c3 - c4 + ca - 4;
     return (2 * t + 9) >> 4;
 }
 
