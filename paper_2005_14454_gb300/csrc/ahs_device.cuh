@@ -174,11 +174,14 @@ static __device__ __noinline__ double wrap_plaq_fp64(In a, In b, In c, In d)
 
 // true when the complex number z = (zr, zi) is too close to the branch cut of arg
 // (the negative real axis, or z = 0) for the sign of its computed imaginary part to
-// decide the branch (float32; FP64 fields use the same margin)
+// decide the branch (float32; FP64 fields use the same margin): zr <= 0 and
+// |zi| <= kTie |zr|, evaluated as the one fused multiply-add kTie zr + |zi| <= 0
+// (which also flags a positive zr so small that kTie zr underflows while zi = 0: a
+// flag only sends the value to the FP64 path)
 template <class R>
 static __device__ __forceinline__ bool near_cut(R zr, R zi)
 {
-    return (zr <= R(0)) && (fabs(zi) <= R(kTie) * fabs(zr));
+    return fma(R(kTie), zr, fabs(zi)) <= R(0);
 }
 
 // Octant code o of an angle in (-pi, pi]: the angle lies in [o pi/4, (o+1) pi/4],
@@ -249,10 +252,16 @@ static __device__ __forceinline__ int winding(int o1, int o2, int o3, int o4, in
 // Both give the winding of the definition: the octants of the exact angles agree with
 // these to within one octant, which the pi/5 margin of winding() absorbs, and at the
 // cut FP64 decides.
+// The code without branches: with b = (zr < 0) and s = (|zi| > |zr|), octant + 4 is
+// 4 + 2b + (b xor s) for zi >= 0 (4, 5 in the first quadrant, 7, 6 in the second),
+// and conjugation maps octant o to -1 - o, i.e. code c to 7 - c -- the same codes as
+// octant() + 4, signed zeros included.
 template <class R>
 static __device__ __forceinline__ int flagged_octant(R zr, R zi)
 {
-    return (octant(zr, zi) + 4) | (near_cut(zr, zi) ? 8 : 0);
+    const int b = zr < R(0), s = fabs(zi) > fabs(zr);
+    const int c = 4 + 2 * b + (b ^ s);
+    return (zi < R(0) ? 7 - c : c) | (near_cut(zr, zi) ? 8 : 0);
 }
 
 // Y_i(x) as a flagged code from V_i = (cos theta_i, sin theta_i): arg of conj(p) U_i q

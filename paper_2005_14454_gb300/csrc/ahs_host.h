@@ -80,7 +80,7 @@ inline StepCoef coefficients(const LatticeParams *h, int64_t n)
     k.wrap = h->wrap;
     k.m_grad = (float)(1.0 / (dx * dx));
     k.m_pot = (float)(0.25 * h->lambda0 * S.c);
-    k.m_el = (float)(1.0 / (2.0 * h->e0 * h->e0 * S.c));
+    k.m_el = (float)(0.25 / (2.0 * h->e0 * h->e0 * S.c));   // applied to the sum of the half-step E
     k.m_mag = (float)(1.0 / (h->e0 * h->e0 * S.c * dx * dx * dx * dx));
     const Scalars P = scalars(h, n - 1);   // the kick that produced the stored momenta
     const double kappa = P.c * (1.0 + P.delta) / (1.0 + P.omega);
@@ -107,7 +107,7 @@ inline StepCoef64 coefficients64(const LatticeParams *h, int64_t n)
     k.wrap = h->wrap;
     k.m_grad = 1.0 / (dx * dx);
     k.m_pot = 0.25 * h->lambda0 * S.c;
-    k.m_el = 1.0 / (2.0 * h->e0 * h->e0 * S.c);
+    k.m_el = 0.25 / (2.0 * h->e0 * h->e0 * S.c);
     k.m_mag = 1.0 / (h->e0 * h->e0 * S.c * dx * dx * dx * dx);
     const Scalars P = scalars(h, n - 1);
     k.m_gauss = 2.0 * h->e0 * h->e0 * P.c * (1.0 + P.delta) / (1.0 + P.omega);

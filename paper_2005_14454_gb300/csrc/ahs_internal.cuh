@@ -57,7 +57,7 @@ struct StepCoef {
     // measurement factors (Eqs. diagxi, diagvel and the Gauss residual)
     float m_grad;   // 1/dx^2
     float m_pot;    // lambda0 c / 4
-    float m_el;     // 1/(2 e0^2 c)
+    float m_el;     // 1/(8 e0^2 c): 1/(2 e0^2 c) times the 1/4 of squaring a mean of two
     float m_mag;    // 1/(e0^2 c dx^4)
     float m_gauss;  // 2 e0^2 kappa_{n-1}
     float inv_dx;

@@ -300,23 +300,24 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
 
             if (MEASURE) {
                 // diagnostics (Eqs. diagxi, diagvel) with explicit roundings: the
-                // momenta at n are the means of those at n -+ 1/2
-                const R half = R(0.5), third = R(1) / R(3), one = R(1);
-                auto mean = [&](R a, R al, R b, R bl) {
-                    return COMP ? rn_mul(half, rn_add(rn_add(a, b), rn_add(al, bl))) : rn_mul(half, rn_add(a, b));
+                // momenta at n are the means of those at n -+ 1/2.  A mean is half the
+                // sum, so its square is a quarter of the sum's -- scalings by powers of
+                // two are exact, so K = |sum|^2 / 4 and El = (m_el / 4) |sum|^2 (m_el
+                // carries the 1/4) give the bits of squaring the means
+                const R quarter = R(0.25), third = R(1) / R(3), one = R(1);
+                auto sum = [&](R a, R al, R b, R bl) {
+                    return COMP ? rn_add(rn_add(a, b), rn_add(al, bl)) : rn_add(a, b);
                 };
                 auto sq2 = [](R a, R b) { return rn_fma(a, a, rn_mul(b, b)); };
-                const R pbr = mean(pe_cur.qr, pe_cur.qrl, qnr, qnrl);
-                const R pbi = mean(pe_cur.qi, pe_cur.qil, qni, qnil);
-                const R K = sq2(pbr, pbi);
+                const R K = rn_mul(quarter, sq2(sum(pe_cur.qr, pe_cur.qrl, qnr, qnrl), sum(pe_cur.qi, pe_cur.qil, qni, qnil)));
                 const R G = rn_mul(k.m_grad, rn_add(rn_add(sq2(rn_sub(hx.x, p0.x), rn_sub(hx.y, p0.y)),
                                                            sq2(rn_sub(hy.x, p0.x), rn_sub(hy.y, p0.y))),
                                                     sq2(rn_sub(hz.x, p0.x), rn_sub(hz.y, p0.y))));
                 const R dm = rn_sub(mod2, k.sigma2);
                 const R V = rn_mul(rn_mul(k.m_pot, dm), dm);
-                const R ebx = mean(pe_cur.ex, pe_cur.exl, enx, enxl);
-                const R eby = mean(pe_cur.ey, pe_cur.eyl, eny, enyl);
-                const R ebz = mean(pe_cur.ez, pe_cur.ezl, enz, enzl);
+                const R ebx = sum(pe_cur.ex, pe_cur.exl, enx, enxl);
+                const R eby = sum(pe_cur.ey, pe_cur.eyl, eny, enyl);
+                const R ebz = sum(pe_cur.ez, pe_cur.ezl, enz, enzl);
                 const R El = rn_mul(k.m_el, rn_fma(ebz, ebz, sq2(ebx, eby)));
                 const R B = rn_mul(k.m_mag, rn_add(rn_add(rn_sub(one, Qxy.x), rn_sub(one, Qxz.x)), rn_sub(one, Qyz.x)));
                 const R L = rn_sub(rn_add(rn_sub(rn_sub(K, G), V), El), B);
