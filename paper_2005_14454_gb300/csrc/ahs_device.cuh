@@ -83,8 +83,8 @@ static __global__ void bounds_selftest_kernel()
 // |th| up to ~1e5; then sin r = r + r^3 S(r^2) and cos r = 1 + r^2 C(r^2) with the
 // near-minimax polynomials of gen_link_sincos.py (degrees 9 and 10), and both
 // change sign for odd k.  Error: at most 1.3e-7 (sin) and 1.5e-7 (cos) absolute,
-// i.e. 1-2 ulp of values near 1; |V|^2 - 1 is unbiased to 4e-9.  No branches and
-// no special-function unit: 17 instructions on the FMA and ALU pipes.
+// i.e. 1-2 ulp of values near 1; |V|^2 - 1 is unbiased to 4e-9.  No branches, no
+// special-function unit and no conversion: 16 instructions on the FMA and ALU pipes.
 constexpr float kLinkS0 = -0.16666659712791443f, kLinkS1 = 0.00833306647837162f,
                 kLinkS2 = -0.0001980959059437737f, kLinkS3 = 2.605750751172309e-06f;
 constexpr float kLinkC0 = -0.5f, kLinkC1 = 0.04166664183139801f, kLinkC2 = -0.00138884037733078f,
@@ -92,10 +92,15 @@ constexpr float kLinkC0 = -0.5f, kLinkC1 = 0.04166664183139801f, kLinkC2 = -0.00
 constexpr float kLinkInvPi = 0.31830987334251404f;   // float32(1/pi)
 constexpr float kLinkPiA = 3.1415927410125732f;      // float32(pi)
 constexpr float kLinkPiB = -8.742277657347586e-08f;  // float32(pi - kLinkPiA)
+constexpr float kLinkRound = 12582912.0f;             // 1.5 * 2^23
 
 static __device__ __forceinline__ void link_sincos(float th, float &s, float &c)
 {
-    const float k = rintf(th * kLinkInvPi);
+    // k = rint(th / pi) by the rounding of one fused multiply-add: t = 1.5 * 2^23 +
+    // th / pi lies in [2^23, 2^24) for |th| < 2^22 pi, where float32 spacing is 1,
+    // so t - 1.5 * 2^23 is the nearest integer and t's last bit is k's parity
+    const float t = fmaf(th, kLinkInvPi, kLinkRound);
+    const float k = t - kLinkRound;
     float r = fmaf(-k, kLinkPiA, th);
     r = fmaf(-k, kLinkPiB, r);
     const float r2 = r * r;
@@ -108,7 +113,7 @@ static __device__ __forceinline__ void link_sincos(float th, float &s, float &c)
     pc = fmaf(r2, pc, kLinkC0);
     const float sv = fmaf(r * r2, ps, r);
     const float cv = fmaf(r2, pc, 1.0f);
-    const unsigned flip = (unsigned)__float2int_rn(k) << 31;   // (-1)^k as a sign bit
+    const unsigned flip = __float_as_uint(t) << 31;   // (-1)^k as a sign bit
     s = __uint_as_float(__float_as_uint(sv) ^ flip);
     c = __uint_as_float(__float_as_uint(cv) ^ flip);
 }

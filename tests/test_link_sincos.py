@@ -29,7 +29,9 @@ def fma(a, b, c):
 def link_sincos(th, K):
     th = th.astype(f32)
     full = lambda v: np.full(th.shape, v, f32)
-    k = np.rint(th * K["kLinkInvPi"]).astype(f32)
+    # k = rint(th / pi) from the rounding of t = 1.5 * 2^23 + th / pi (one FMA)
+    t = fma(th, full(K["kLinkInvPi"]), full(K["kLinkRound"]))
+    k = (t - K["kLinkRound"]).astype(f32)
     r = fma(-k, full(K["kLinkPiA"]), th)
     r = fma(-k, full(K["kLinkPiB"]), r)
     r2 = (r * r).astype(f32)
@@ -42,7 +44,8 @@ def link_sincos(th, K):
     pc = fma(r2, pc, full(K["kLinkC0"]))
     sv = fma((r * r2).astype(f32), ps, r)
     cv = fma(r2, pc, full(1.0))
-    sign = np.where(k.astype(np.int64) % 2 == 1, f32(-1), f32(1))
+    sign = np.where(t.view(np.uint32) & 1, f32(-1), f32(1))   # t's last bit: k's parity
+    assert np.array_equal(t.view(np.uint32) & 1, k.astype(np.int64) & 1)
     return sv * sign, cv * sign
 
 
