@@ -213,14 +213,20 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
             if (ringRow) Syz[qh] = plaquette(by, bz, pc.vz[rby], pn.vy[rb]).y;
             else Sxz[qh] = plaquette(bx, bz, pc.vz[rbx], pn.vx[rb]).y;
         }
+        V2 hzB = Real<R>::v2(0, 0);
+        R jzB = 0;
         if (MEASURE && zz >= z0) {
             // link phases Y_i of plane zz on the tile (Y_x, Y_y carried from the
-            // previous plane) and on its forward ring; old E of the backward ring
+            // previous plane) and on its forward ring; old E of the backward ring.
+            // Y_z = arg(conj(phi) U_z phi(x+z)) from the hop U_z phi(x+z) and the
+            // current J_z = Im(conj(phi) U_z phi(x+z)) the kick of phase C uses
             const int wi = T::w(tx, ty);
-            const V2 p0 = pc.ph[r0], pz = pn.ph[r0];
+            const V2 p0 = pc.ph[r0];
+            hzB = cmulc(pn.ph[r0], vz0);
+            jzB = p0.x * hzB.y - p0.y * hzB.x;
             Syx[wi] = YxCar;
             Syy[wi] = YyCar;
-            Syzw[wi] = link_code(p0.x, p0.y, pz.x, pz.y, vz0.x, vz0.y);
+            Syzw[wi] = flagged_octant(p0.x * hzB.x + p0.y * hzB.y, jzB);
             if (gauss) {
                 Sex[T::q(tx, ty)] = pe_cur.ex;
                 Sey[T::q(tx, ty)] = pe_cur.ey;
@@ -262,7 +268,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
             // forward hops U_i(x) phi(x+i) = conj(V_i) phi(x+i)
             const V2 hx = cmulc(pc.ph[rxp], vx0);
             const V2 hy = cmulc(pc.ph[ryp], vy0);
-            const V2 hz = cmulc(pn.ph[r0], vz0);
+            const V2 hz = MEASURE ? hzB : cmulc(pn.ph[r0], vz0);
             // backward hops U_i(x-i)^* phi(x-i) = V_i(x-i) phi(x-i)
             const V2 bxh = cmul(pc.vx[rxm], pc.ph[rxm]);
             const V2 byh = cmul(pc.vy[rym], pc.ph[rym]);
@@ -282,7 +288,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
             // currents J_i = Im(conj(phi) U_i phi(x+i))
             const R jx = p0.x * hx.y - p0.y * hx.x;
             const R jy = p0.x * hy.y - p0.y * hy.x;
-            const R jz = p0.x * hz.y - p0.y * hz.x;
+            const R jz = MEASURE ? jzB : p0.x * hz.y - p0.y * hz.x;
             const R sxy = Qxy.y, sxz = Qxz.y, syz = Qyz.y;
             const R cxv = -(sxy - Sxy[T::q(tx, ty - 1)]) - (sxz - sxzPrev);
             const R cyv = (sxy - Sxy[T::q(tx - 1, ty)]) - (syz - syzPrev);
