@@ -121,8 +121,8 @@ static __device__ __forceinline__ void link_sincos(float th, float &s, float &c)
 // The FP64 precision mode's link phases, built the same way in double: pi in two
 // FP64 parts, sin r = r + r^3 S(r^2) and cos r = 1 + r^2 C(r^2) of degrees 17 and
 // 16 (gen_link_sincos.py --double; fit errors 3e-19 and 4e-18), sign flipped for
-// odd k.  Error about 1 ulp of values near 1 for |th| up to ~1e5; 25 FP64
-// instructions, no branches.
+// odd k.  Error about 1 ulp of values near 1 for |th| up to ~1e5; 24 FP64
+// instructions, no branches and no conversion.
 __device__ constexpr double kLinkS64[8] = {-0.16666666666666666,     0.008333333333333194,   -0.0001984126984120922,
                                 2.7557319211137538e-06,   -2.505210687282421e-08, 1.6058939706909938e-10,
                                 -7.642991513761023e-13,   2.7211752032504598e-15};
@@ -132,10 +132,13 @@ __device__ constexpr double kLinkC64[8] = {-0.49999999999999983,     0.041666666
 constexpr double kLinkInvPi64 = 0.3183098861837907;        // double(1/pi)
 constexpr double kLinkPiA64 = 3.141592653589793;           // double(pi)
 constexpr double kLinkPiB64 = 1.2246467991473532e-16;      // double(pi - kLinkPiA64)
+constexpr double kLinkRound64 = 6755399441055744.0;         // 1.5 * 2^52
 
 static __device__ __forceinline__ void link_sincos(double th, double &s, double &c)
 {
-    const double k = rint(th * kLinkInvPi64);
+    // k = rint(th / pi) and its parity from one fused multiply-add, as in float32
+    const double t = fma(th, kLinkInvPi64, kLinkRound64);
+    const double k = t - kLinkRound64;
     double r = fma(-k, kLinkPiA64, th);
     r = fma(-k, kLinkPiB64, r);
     const double r2 = r * r;
@@ -147,7 +150,7 @@ static __device__ __forceinline__ void link_sincos(double th, double &s, double 
     }
     const double sv = fma(r * r2, ps, r);
     const double cv = fma(r2, pc, 1.0);
-    const unsigned long long flip = (unsigned long long)(__double2int_rn(k) & 1) << 63;
+    const unsigned long long flip = (unsigned long long)__double_as_longlong(t) << 63;
     s = __longlong_as_double(__double_as_longlong(sv) ^ (long long)flip);
     c = __longlong_as_double(__double_as_longlong(cv) ^ (long long)flip);
 }

@@ -119,9 +119,13 @@ def test_double_polynomials_fit_and_reduction():
         worst_c = max(worst_c, float(abs((1 + r2 * pc) - mp.cos(r))))
     assert worst_s < 1e-17 and worst_c < 5e-17         # cos: the FP64 rounding of C0 ~ -1/2
     th = np.random.default_rng(9).uniform(-1e4, 1e4, 3000)
-    k = np.rint(th * sc["kLinkInvPi64"])
-    # the two fused multiply-adds of the reduction, each rounded once
+    # the fused multiply-adds of the reduction, each rounded once: k = rint(th / pi)
+    # from t = 1.5 * 2^52 + th / pi, whose last bit is k's parity
     fma = lambda a, b_, c: float(mp.mpf(a) * mp.mpf(b_) + mp.mpf(c))
+    t = np.array([fma(x, sc["kLinkInvPi64"], sc["kLinkRound64"]) for x in th])
+    k = t - sc["kLinkRound64"]
+    assert sc["kLinkRound64"] == 1.5 * 2.0 ** 52
+    assert np.array_equal(t.view(np.int64) & 1, k.astype(np.int64) & 1)
     r = np.array([fma(-kk, sc["kLinkPiB64"], fma(-kk, sc["kLinkPiA64"], t)) for kk, t in zip(k, th)])
     r2 = r * r
     ps = np.full_like(r, S[7]); pc = np.full_like(r, C[7])
