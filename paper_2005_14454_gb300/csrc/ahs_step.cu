@@ -196,9 +196,13 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         // ---- B: plaquettes of plane zz (tile + backward ring)
         const int r0 = T::r(tx, ty), rxp = T::r(tx + 1, ty), ryp = T::r(tx, ty + 1);
         const V2 vx0 = pc.vx[r0], vy0 = pc.vy[r0], vz0 = pc.vz[r0];
+        // plane zz+1 at the own site (written by this thread in phase A): kept for the
+        // measurement's link phases of plane zz+1 after the barrier
+        const V2 vxn = pn.vx[r0], vyn = pn.vy[r0];
+        const V2 pn0 = MEASURE ? pn.ph[r0] : Real<R>::v2(0, 0);
         const V2 Qxy = plaquette(vx0, vy0, pc.vy[rxp], pc.vx[ryp]);
-        const V2 Qxz = plaquette(vx0, vz0, pc.vz[rxp], pn.vx[r0]);
-        const V2 Qyz = plaquette(vy0, vz0, pc.vz[ryp], pn.vy[r0]);
+        const V2 Qxz = plaquette(vx0, vz0, pc.vz[rxp], vxn);
+        const V2 Qyz = plaquette(vy0, vz0, pc.vz[ryp], vyn);
         {
             const int qi0 = T::q(tx, ty);
             Sxy[qi0] = Qxy.y;
@@ -222,7 +226,7 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
             // current J_z = Im(conj(phi) U_z phi(x+z)) the kick of phase C uses
             const int wi = T::w(tx, ty);
             const V2 p0 = pc.ph[r0];
-            hzB = cmulc(pn.ph[r0], vz0);
+            hzB = cmulc(pn0, vz0);
             jzB = p0.x * hzB.y - p0.y * hzB.x;
             Syx[wi] = YxCar;
             Syy[wi] = YyCar;
@@ -255,7 +259,6 @@ __device__ __forceinline__ void tile_step(typename Tile<BY, typename FA::real>::
         // (ragged-tile columns too: they are the periodic images the ring reads)
         int YxNext = 0, YyNext = 0;
         if (MEASURE) {
-            const V2 pn0 = pn.ph[r0], vxn = pn.vx[r0], vyn = pn.vy[r0];
             const V2 qxn = pn.ph[rxp], qyn = pn.ph[ryp];
             YxNext = link_code(pn0.x, pn0.y, qxn.x, qxn.y, vxn.x, vxn.y);
             YyNext = link_code(pn0.x, pn0.y, qyn.x, qyn.y, vyn.x, vyn.y);
