@@ -109,12 +109,38 @@ __device__ void reduce_rows(const double *__restrict__ part, int nb, const ObsSc
     double v[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) v[q] = 0.0;
-    for (int b = t; b < nb; b += RT) {
+    auto add = [&](const double *x) {
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const double x = part[(size_t)b * NQ + q];
-            v[q] = (q == Q_GMAX) ? fmax(v[q], x) : v[q] + x;
+        for (int q = 0; q < NQ; ++q) v[q] = (q == Q_GMAX) ? fmax(v[q], x[q]) : v[q] + x[q];
+    };
+    // rows t, t + RT, t + 2 RT, ... in that order; four rows' loads are issued
+    // before their additions (a row is 16 doubles, 128-byte aligned: 8 x 16 bytes)
+    int b = t;
+    for (; b + 3 * RT < nb; b += 4 * RT) {
+        double x[4][NQ];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const double2 *row = reinterpret_cast<const double2 *>(part + (size_t)(b + k * RT) * NQ);
+#pragma unroll
+            for (int h = 0; h < NQ / 2; ++h) {
+                const double2 d = __ldg(row + h);
+                x[k][2 * h] = d.x;
+                x[k][2 * h + 1] = d.y;
+            }
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) add(x[k]);
+    }
+    for (; b < nb; b += RT) {
+        double x[NQ];
+        const double2 *row = reinterpret_cast<const double2 *>(part + (size_t)b * NQ);
+#pragma unroll
+        for (int h = 0; h < NQ / 2; ++h) {
+            const double2 d = __ldg(row + h);
+            x[2 * h] = d.x;
+            x[2 * h + 1] = d.y;
+        }
+        add(x);
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) sh[t][q] = v[q];
